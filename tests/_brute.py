@@ -1,0 +1,91 @@
+"""Independent brute-force restatement of the forward model for tiny inputs.
+
+Used only to pin the FP64 C oracle. It is written differently on purpose:
+spaxel membership by exact rational arithmetic, bilinear interpolation by
+scipy's RegularGridInterpolator, Doppler resampling by numpy.interp on the
+zero-extended template, per-voxel sums by an explicit membership test, and the
+PSF/LSF by scipy.ndimage.convolve with zero padding. The kernel weights are
+written out from the Gaussian formula here, independently of the oracle.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+import math
+
+import numpy as np
+from scipy.interpolate import RegularGridInterpolator
+from scipy.ndimage import convolve
+
+C_KMS = 299792.458
+
+
+def exact_spaxel(xp: float, yp: float, tel):
+    """Spaxel (ix, iy) by exact rational arithmetic, None if outside."""
+    size = Fraction(tel.spaxel_size)
+    x_lo = -Fraction(tel.nx) * size / 2
+    y_lo = -Fraction(tel.ny) * size / 2
+    u = (Fraction(xp) - x_lo) / size
+    w = (Fraction(yp) - y_lo) / size
+    if 0 <= u < tel.nx and 0 <= w < tel.ny:
+        return int(math.floor(u)), int(math.floor(w)), u, w
+    return None
+
+
+def projected(p):
+    if p.preprojected:
+        return (p.x.astype(np.float64), p.y.astype(np.float64), p.v_los.astype(np.float64))
+    ci, si = math.cos(p.inclination), math.sin(p.inclination)
+    y = p.y.astype(np.float64); z = p.z.astype(np.float64)
+    return (p.x.astype(np.float64), y * ci - z * si,
+            p.vy.astype(np.float64) * si + p.vz.astype(np.float64) * ci)
+
+
+def particle_spectrum(ssp, tel, mass, age, Z, v, spectra=None):
+    """m * T_interp(lambda_j / dop), T_interp bilinear in (log age, log Z), clamped,
+    and linear in wavelength with one zero node appended on either side."""
+    sp = ssp.spectra if spectra is None else spectra
+    la = np.clip(math.log10(age), ssp.log10_age_nodes[0], ssp.log10_age_nodes[-1])
+    lz = np.clip(math.log10(Z), ssp.log10_Z_nodes[0], ssp.log10_Z_nodes[-1])
+    interp = RegularGridInterpolator((ssp.log10_age_nodes, ssp.log10_Z_nodes), sp, method="linear")
+    T = interp([[la, lz]])[0]
+    lam_s = ssp.lambda0 + ssp.dlambda * np.arange(-1, ssp.n_lambda + 1)
+    T_ext = np.concatenate([[0.0], T, [0.0]])
+    lam = tel.lambda0 + tel.dlambda * np.arange(tel.n_lambda)
+    lam_rest = lam / ((1.0 + tel.z_cosmo) * (1.0 + v / C_KMS))
+    return tel.flux_scale * mass * np.interp(lam_rest, lam_s, T_ext, left=0.0, right=0.0)
+
+
+def cube0(p, ssp, tel, spectra=None):
+    xp, yp, v = projected(p)
+    spec = [particle_spectrum(ssp, tel, float(p.mass[i]), float(p.age[i]), float(p.Z[i]), v[i],
+                              spectra) for i in range(p.n)]
+    where = [exact_spaxel(xp[i], yp[i], tel) for i in range(p.n)]
+    cube = np.zeros((tel.ny, tel.nx, tel.n_lambda))
+    for iy in range(tel.ny):
+        for ix in range(tel.nx):
+            for i in range(p.n):
+                if where[i] is not None and where[i][0] == ix and where[i][1] == iy:
+                    cube[iy, ix] += spec[i]
+    return cube
+
+
+def gauss_weights(sigma: float, radius: int):
+    d = np.arange(-radius, radius + 1, dtype=np.float64)
+    g = np.exp(-0.5 * (d / sigma) ** 2)
+    return g / g.sum()
+
+
+def psf_lsf(cube, tel):
+    out = cube
+    if tel.psf_fwhm > 0:
+        s = tel.psf_fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+        r = tel.psf_radius if tel.psf_radius > 0 else math.ceil(4 * s)
+        g = gauss_weights(s, r)
+        k = np.outer(g, g)[:, :, None]
+        out = convolve(out, k, mode="constant", cval=0.0)
+    if tel.lsf_sigma > 0:
+        s = tel.lsf_sigma / tel.dlambda
+        r = tel.lsf_radius if tel.lsf_radius > 0 else math.ceil(4 * s)
+        h = gauss_weights(s, r)[None, None, :]
+        out = convolve(out, h, mode="constant", cval=0.0)
+    return out
