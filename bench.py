@@ -1,0 +1,337 @@
+"""Benchmark of the particle -> IFU cube forward model on GB300.
+
+One step = one full forward (orient + spaxel keys, sort, SSP lookup + Doppler
+resampling + per-spaxel deposit, FP64 combine, PSF + LSF) of the mid-size
+galaxy workload: 1e6 star particles (exponential disk), SSP grid 50 ages x 10
+metallicities x 3721 wavelengths in FP32, IFU of 150 x 150 spaxels of 0.2 kpc
+x 3721 bins of 1.25 A from 4750 A, Gaussian PSF (FWHM 1.5 spaxels) and LSF
+(sigma 1.2 A). Metric: particle-wavelength deposits per second (in-field
+particles x wavelength bins / step time), with p50/p99 cube latency.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank forward-models its own galaxy on its own GPU
+(independent problems, no data-path collective: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-wavelength deposits/s and p50/p99 cube latency at stated rel err"
+UNIT = "deposits/s"
+FLOPS_PER_DEPOSIT = 16  # 4 SSP corners x 2 wavelength neighbours, one FMA each
+REL_ERR_BOUND = 1e-5
+# DRAM bytes (read + write) per deposit launch on the mid-size workload, from the
+# ncu capture summarised in profiles/; None until captured for the current kernel.
+DEPOSIT_TRAFFIC_BYTES = None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, target_s: float, seed: int = 123):
+    """Time the oracle's deposit over a seeded set of spaxel neighbourhoods sized
+    for roughly target_s seconds; returns (deposits/s, cores, description,
+    centres, cube0 for the sample, key)."""
+    import oracle
+    tel = wl.telescope
+    p = wl.particles
+    cores = os.cpu_count() or 1
+    xp, yp, v = oracle.orient(p)
+    key = oracle.spaxel_keys(xp, yp, tel)
+    n_s = tel.nx * tel.ny
+    counts = np.bincount(key, minlength=n_s + 1)[:n_s]
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(n_s)
+
+    def mask_for(cs):
+        m = np.zeros(n_s, np.uint8)
+        for s in cs:
+            y, x = divmod(int(s), tel.nx)
+            for yy in range(max(0, y - 3), min(tel.ny, y + 4)):
+                m[yy * tel.nx + max(0, x - 3): yy * tel.nx + min(tel.nx, x + 4)] = 1
+        return m
+
+    # calibrate on a small sample
+    cal = order[:4]
+    m = mask_for(cal)
+    t0 = time.perf_counter()
+    oracle.deposit(key, v, p, wl.ssp, tel, mask=m, n_threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rate = counts[m == 1].sum() * tel.n_lambda / dt
+    budget = rate * target_s
+    cs, tot = [], 0
+    m = np.zeros(n_s, np.uint8)
+    for s in order:
+        cs.append(s)
+        m = mask_for(cs) if len(cs) % 8 == 0 else m
+        tot = counts[mask_for(cs) == 1].sum() * tel.n_lambda if len(cs) % 8 == 0 else tot
+        if tot >= budget or len(cs) >= n_s:
+            break
+    m = mask_for(cs)
+    dep = int(counts[m == 1].sum()) * tel.n_lambda
+    t0 = time.perf_counter()
+    cube0 = oracle.deposit(key, v, p, wl.ssp, tel, mask=m, n_threads=cores)
+    dt = time.perf_counter() - t0
+    desc = (f"FP64 oracle deposit over {int(m.sum())} of {n_s} spaxels (7x7 neighbourhoods of "
+            f"{len(cs)} seeded centres), {int(counts[m == 1].sum())} particles x {tel.n_lambda} bins")
+    return dep / dt, cores, desc, np.array(cs, dtype=np.int32), cube0, dep, dt
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2412_08265_gb300 import synth
+    wl = synth.mid_galaxy()
+    times, deps = [], []
+    per_step = max(3.0, 60.0 / max(args.steps + args.warmup, 1))
+    for i in range(args.warmup + args.steps):
+        rate, cores, desc, _, _, dep, dt = oracle_sample(wl, per_step, seed=1000 + i)
+        if i >= args.warmup:
+            times.append(dt)
+            deps.append(dep)
+    value = float(sum(deps) / sum(times))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "n_particles": wl.particles.n, "spaxels": "150x150",
+                       "n_lambda": 3721, "ssp": "50x10x3721", "sample": "bounded spaxel subset per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_2412_08265_gb300 import synth
+    from paper_2412_08265_gb300.model import CubeModel
+    from paper_2412_08265_gb300 import capi
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = synth.mid_galaxy(seed=1 + rank)
+    model = CubeModel(wl.ssp, wl.telescope, "f32", max_particles=wl.particles.n, device=dev)
+    d = model.device_particles(wl.particles)
+    out = torch.empty(model.cube_shape, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        model.forward(d, out=out)
+    torch.cuda.synchronize()
+    st = model.stats()
+    n_in, deposits, launches_per_step = st["n_in_fov"], st["deposits"], st["kernel_launches"]
+
+    model.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dep_ms = []
+    clocks = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))           # evict L2 between timed steps (outside the events)
+        ev[i][0].record(stream)
+        model.forward(d, out=out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    dep_ms = model.profile_history("deposit")
+    stage_last = model.stage_times()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    total_s = float(step_ms.sum()) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = deposits * args.steps * ws / total_s
+    model.set_profiling(False)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if rank == 0:
+        p = wl.particles
+        host = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), dtype=np.float32)).pin_memory()
+                for k in ("x", "y", "v_los", "mass", "age", "Z")}
+        cp = model.c_particles({**{k: v.numpy() for k, v in host.items()}, "preprojected": True,
+                                "inclination": 0.0}, on_device=False)
+        hcube = torch.empty(model.cube_shape, dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * 4 for v in host.values())
+        d2h = hcube.numel() * 4
+        for _ in range(2):
+            capi.rubix_cube_forward(model.handle, cp, 0, 0.0, hcube.data_ptr(), 0, stream.cuda_stream)
+        k_e2e = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            capi.rubix_cube_forward(model.handle, cp, 0, 0.0, hcube.data_ptr(), 0, stream.cuda_stream)
+        t_e2e = (time.perf_counter() - t0) / k_e2e
+        e2e = {"value": deposits / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (deposit) ----
+    peaks = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
+    peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    dep_avg_s = float(np.mean(dep_ms)) / 1e3
+    achieved = deposits * FLOPS_PER_DEPOSIT / dep_avg_s / 1e12
+    traffic = DEPOSIT_TRAFFIC_BYTES
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": traffic,
+            "kernel": "k_deposit", "kernel_ms": 1e3 * dep_avg_s,
+            "peak_basis": f"FP32 FMA pipe: {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+            "deposits_per_launch": deposits, "flops_per_deposit": FLOPS_PER_DEPOSIT}
+
+    # ---- CPU baseline: the oracle on a bounded sample, and the sampled rel err ----
+    cpu = None
+    rel = None
+    if not args.no_cpu_baseline:
+        import oracle
+        rate, cores, desc, centres, cube0, dep, dt = oracle_sample(wl, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        ref = oracle.psf_lsf_at(cube0, wl.telescope, centres[: min(len(centres), 24)])
+        got = out.reshape(-1, wl.telescope.n_lambda)[torch.from_numpy(centres[: min(len(centres), 24)]).long().to(dev)]
+        got = got.cpu().numpy().astype(np.float64)
+        rel = float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "n_particles": wl.particles.n, "n_in_fov": n_in,
+                       "spaxels": "150x150", "spaxel_kpc": 0.2, "n_lambda": 3721, "ssp": "50x10x3721 f32",
+                       "psf_fwhm_spaxels": 1.5, "lsf_sigma_A": 1.2, "l2": "flushed between timed steps",
+                       "parallelism": f"replicas x{ws}"},
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "rel_err_bound": REL_ERR_BOUND, "rel_err_sampled": rel,
+            "particles_per_s": n_in * args.steps * ws / total_s,
+            "clocks": clk, "gpu_launches": int(launches_per_step * args.steps),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "stage_ms_last_step": stage_last}
+    print(json.dumps(line), flush=True)
+    model.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

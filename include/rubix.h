@@ -1,0 +1,191 @@
+/*
+ * rubix.h -- C ABI of the GB300 (sm_103a) particle -> IFU data-cube forward
+ * model of RUBIX (arXiv 2412.08265). Every step of the pipeline runs in the
+ * library's own CUDA kernels; callers pass plain host or device pointers.
+ *
+ * The pipeline (Sec. 3 "RUBIX Codebase" of the paper):
+ *   orient the galaxy in the field of view -> assign particles to spaxels ->
+ *   look each star's spectrum up in an SSP library -> Doppler shift by the
+ *   line-of-sight velocity -> resample onto the telescope wavelength grid ->
+ *   sum the spectra in each spaxel -> convolve with a Gaussian PSF and LSF
+ *   (Sec. 4) -> add noise.  Gradients through the pipeline (Abstract, Sec. 1)
+ *   are provided by rubix_cube_backward.
+ *
+ * Readings of the steps the paper leaves unspecified (all implemented exactly
+ * this way by the library):
+ *   - Orientation: rotation about the x axis by the inclination i:
+ *       x' = x, y' = y cos i - z sin i, v_los = vy sin i + vz cos i
+ *     (FP64, each product and sum rounded once; cos i, sin i from the host).
+ *   - Spaxels: nx*ny squares of side spaxel_size centred on (0, 0), half-open;
+ *     x_lo = (-0.5*nx)*size, u = (x' - x_lo) * (1/size) in FP64, ix = floor(u).
+ *     Particles outside the field are dropped.
+ *   - SSP lookup: bilinear in (log10 age/Gyr, log10 Z), clamped at the grid.
+ *   - Doppler + resampling: rest wavelength of output bin j is
+ *     (lambda0 + j*dlambda) / ((1 + z_cosmo)(1 + v_los/c)); the template is
+ *     linearly interpolated there, and is zero outside its wavelength range.
+ *   - Spectrum of a particle = flux_scale * mass * interpolated template.
+ *   - PSF: 2-D Gaussian, sigma = FWHM / (2 sqrt(2 ln 2)) spaxels; LSF: 1-D
+ *     Gaussian, sigma = lsf_sigma / dlambda bins; both sampled at integer
+ *     offsets up to r = ceil(4 sigma), normalised to 1, zero padded, PSF first.
+ *   - Noise: cube + |cube| / S2N * N(0, 1), N(0,1) from Philox4x32-10 keyed by
+ *     the seed, counter = voxel index, Box-Muller.
+ *
+ * Conventions
+ *   - Every call returns a rubix_status; rubix_last_error_message() gives a
+ *     thread-local description of the last failure. No exception crosses the ABI.
+ *   - The caller owns every buffer it passes. Handles own their device copies
+ *     of the SSP grid, their scratch space and the state kept for backward.
+ *   - A handle is not thread safe: use one handle per host thread / stream.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work is enqueued on it; calls return without waiting unless
+ *     they must return host data.
+ *   - Cube layout: float32 [ny][nx][n_lambda], wavelength fastest.
+ */
+#ifndef RUBIX_H
+#define RUBIX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rubix_status;
+#define RUBIX_OK 0
+#define RUBIX_ERR_INVALID_ARG 1
+#define RUBIX_ERR_OOM 2
+#define RUBIX_ERR_CUDA 3
+#define RUBIX_ERR_TIMEOUT 4
+#define RUBIX_ERR_REJECTED 5
+#define RUBIX_ERR_CANCELLED 6
+#define RUBIX_ERR_NOT_READY 7
+#define RUBIX_ERR_UNSUPPORTED 8
+#define RUBIX_ERR_DEVICE 9 /* a kernel reported an internal error (e.g. a bounded wait expired) */
+
+/* Storage type of the SSP templates on the device (arithmetic is FP32). */
+#define RUBIX_F32 0
+#define RUBIX_BF16 1
+#define RUBIX_F16 2
+
+/* SSP library (Sec. 3: "a lookup from a simple stellar population library").
+ * All pointers are HOST pointers, read during rubix_cube_create only. */
+typedef struct rubix_ssp_grid {
+    int32_t n_age, n_Z, n_lambda;   /* grid sizes, each >= 1; n_lambda >= 2 */
+    const double *log10_age_nodes;  /* [n_age], strictly increasing, log10(age / Gyr) */
+    const double *log10_Z_nodes;    /* [n_Z], strictly increasing, log10(Z) */
+    double lambda0, dlambda;        /* template wavelengths lambda0 + k*dlambda, Angstrom */
+    const double *spectra;          /* [n_age][n_Z][n_lambda], luminosity per unit mass */
+    int32_t storage_dtype;          /* RUBIX_F32 | RUBIX_BF16 | RUBIX_F16 */
+} rubix_ssp_grid;
+
+/* Telescope / IFU (Sec. 3: "accounting for telescope-specific configurations";
+ * Sec. 4: Gaussian PSF and LSF). */
+typedef struct rubix_telescope {
+    int32_t nx, ny;                 /* spaxels, each >= 1, nx*ny < 2^24 */
+    double spaxel_size;             /* kpc, > 0 */
+    int32_t n_lambda;               /* output bins, >= 1 */
+    double lambda0, dlambda;        /* bin centres lambda0 + j*dlambda, Angstrom, dlambda > 0 */
+    double psf_fwhm;                /* spaxels; 0 = no PSF */
+    double lsf_sigma;               /* Angstrom; 0 = no LSF */
+    int32_t psf_radius, lsf_radius; /* kernel radii; <= 0 means ceil(4 sigma); each <= 64 */
+    double z_cosmo;                 /* cosmological redshift of the galaxy (usually 0) */
+    double flux_scale;              /* multiplies every spectrum (e.g. 1/(4 pi d_L^2)); 1 = none */
+} rubix_telescope;
+
+/* Star particles (Sec. 3: input handler fields), float32 structure of arrays.
+ * preprojected = 1: x, y are sky-plane positions (kpc) and v_los (km/s) is
+ *                   given; z, vx, vy, vz are ignored (may be NULL).
+ * preprojected = 0: x, y, z (kpc) and vx, vy, vz (km/s) are 3-D; the galaxy
+ *                   is inclined by `inclination` radians about the x axis.
+ * mass: Msun; age: Gyr (> 0); Z: metal mass fraction (> 0).
+ * on_device = 1: all pointers are device pointers; 0: host pointers (copied
+ * to the device inside the call; pinned memory makes the copy asynchronous). */
+typedef struct rubix_particles {
+    int64_t n;
+    const float *x, *y, *z, *vx, *vy, *vz, *v_los;
+    const float *mass, *age, *Z;
+    int32_t on_device;
+    int32_t preprojected;
+    double inclination;
+} rubix_particles;
+
+typedef struct rubix_cube rubix_cube_t;
+typedef struct rubix_server rubix_server_t;
+
+/* Create a forward-model handle for one SSP grid and one telescope.
+ * Copies the SSP grid to the device in its storage dtype (rows padded to 16 B)
+ * and reserves scratch for up to `max_particles` particles (grown on demand).
+ * Errors: INVALID_ARG (bad sizes, non-increasing nodes, NULL pointers),
+ * OOM, CUDA. On error *out is NULL. Uses the current CUDA device. */
+rubix_status rubix_cube_create(const rubix_ssp_grid *ssp, const rubix_telescope *tel,
+                               int64_t max_particles, rubix_cube_t **out);
+
+/* Forward model (Sec. 3 pipeline): particles -> cube_out [ny][nx][n_lambda].
+ * cube_out is a device pointer if cube_on_device = 1, else a host pointer
+ * (the call then waits for the device-to-host copy). noise_s2n <= 0 turns the
+ * noise off; noise_seed selects the Philox stream. Deterministic: the same
+ * inputs give bitwise the same cube. The sorted particle order and setup of
+ * this call are kept for rubix_cube_backward.
+ * Errors: INVALID_ARG, OOM (scratch growth), CUDA, DEVICE. */
+rubix_status rubix_cube_forward(rubix_cube_t *h, const rubix_particles *p, uint64_t noise_seed,
+                                float noise_s2n, float *cube_out, int32_t cube_on_device,
+                                void *stream);
+
+/* Adjoint of the most recent noiseless forward on this handle (gradients
+ * through the pipeline, Abstract / Sec. 1). dL_dcube: device pointer, float32
+ * [ny][nx][n_lambda]. Outputs (device pointers, float32 [n], original particle
+ * order, any may be NULL): dL/dmass, dL/dage (per Gyr), dL/dZ, dL/dv_los
+ * (per km/s). Out-of-field particles get 0. d_global (device, nullable,
+ * float64[2]): [0] = dL/dv_sys (a systemic velocity added to every particle)
+ * = sum of dL/dv_los; [1] = dL/dln(M) for a global mass scale = sum of
+ * mass * dL/dmass, both summed in FP64 in a fixed order.
+ * Errors: INVALID_ARG (no forward yet, or the forward used noise), CUDA. */
+rubix_status rubix_cube_backward(rubix_cube_t *h, const float *dL_dcube, float *d_mass,
+                                 float *d_age, float *d_Z, float *d_vlos, double *d_global,
+                                 void *stream);
+
+rubix_status rubix_cube_destroy(rubix_cube_t *h);
+
+/* Spaxel assignment only (orientation + key, bit-exact definition above):
+ * keys_out (device int32 [n]) gets iy*nx + ix, or nx*ny for particles outside. */
+rubix_status rubix_cube_spaxel_keys(rubix_cube_t *h, const rubix_particles *p, int32_t *keys_out,
+                                    void *stream);
+
+/* Copy the sort result of the most recent forward (device pointers):
+ * perm_out int32 [n]: particle indices ordered by spaxel key, ties by index;
+ * seg_off_out int32 [nx*ny + 2]: first sorted position of each key, then n.
+ * Either may be NULL. */
+rubix_status rubix_cube_sorted(rubix_cube_t *h, int32_t *perm_out, int32_t *seg_off_out,
+                               void *stream);
+
+/* Per-stage device times (milliseconds) of the most recent forward, measured
+ * with CUDA events on the forward's stream when profiling is on. Order:
+ * [0] assign+sort, [1] particle setup + work list, [2] deposit, [3] combine,
+ * [4] PSF+LSF+noise, [5] whole forward. Waits for the forward to finish.
+ * n_inout: capacity in, number written out. */
+rubix_status rubix_cube_set_profiling(rubix_cube_t *h, int32_t enable);
+rubix_status rubix_cube_stage_times(rubix_cube_t *h, float *ms, int32_t *n_inout);
+
+/* Time of one stage (index as above) for every forward enqueued since
+ * profiling was last enabled (at most 256, oldest first), without waiting
+ * between forwards while they are enqueued; waits for them here. */
+rubix_status rubix_cube_profile_history(rubix_cube_t *h, int32_t stage, float *ms, int32_t *n_inout);
+
+/* Counters of the most recent forward (waits for it): [0] particles in the
+ * field, [1] deposits = in-field particles * n_lambda, [2] particles on the
+ * slow (out-of-slab Doppler range) path, [3] number of deposit launches,
+ * [4] kernels launched by the forward. n_inout: capacity in, written out. */
+rubix_status rubix_cube_stats(rubix_cube_t *h, int64_t *stats, int32_t *n_inout);
+
+/* Thread-local message for the last non-OK status returned on this thread. */
+const char *rubix_last_error_message(void);
+
+/* Library version string. */
+const char *rubix_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RUBIX_H */

@@ -1,0 +1,180 @@
+"""ctypes binding of the C ABI declared in include/rubix.h (argument marshalling only).
+
+The Python functions carry the C names (``rubix_cube_create``,
+``rubix_cube_forward`` ...) and take the same arguments; every step of the
+computation runs in the library's CUDA kernels. The library must have been
+built (``paper_2412_08265_gb300.build.build()``); loading fails loudly
+otherwise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "librubix.so")
+
+RUBIX_OK = 0
+RUBIX_ERR_INVALID_ARG = 1
+RUBIX_ERR_OOM = 2
+RUBIX_ERR_CUDA = 3
+RUBIX_ERR_TIMEOUT = 4
+RUBIX_ERR_REJECTED = 5
+RUBIX_ERR_CANCELLED = 6
+RUBIX_ERR_NOT_READY = 7
+RUBIX_ERR_UNSUPPORTED = 8
+RUBIX_ERR_DEVICE = 9
+
+RUBIX_F32, RUBIX_BF16, RUBIX_F16 = 0, 1, 2
+DTYPES = {"f32": RUBIX_F32, "bf16": RUBIX_BF16, "f16": RUBIX_F16}
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+
+
+class rubix_ssp_grid(C.Structure):
+    _fields_ = [("n_age", C.c_int32), ("n_Z", C.c_int32), ("n_lambda", C.c_int32),
+                ("log10_age_nodes", C.c_void_p), ("log10_Z_nodes", C.c_void_p),
+                ("lambda0", C.c_double), ("dlambda", C.c_double), ("spectra", C.c_void_p),
+                ("storage_dtype", C.c_int32)]
+
+
+class rubix_telescope(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("spaxel_size", C.c_double),
+                ("n_lambda", C.c_int32), ("lambda0", C.c_double), ("dlambda", C.c_double),
+                ("psf_fwhm", C.c_double), ("lsf_sigma", C.c_double), ("psf_radius", C.c_int32),
+                ("lsf_radius", C.c_int32), ("z_cosmo", C.c_double), ("flux_scale", C.c_double)]
+
+
+class rubix_particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p), ("v_los", C.c_void_p),
+                ("mass", C.c_void_p), ("age", C.c_void_p), ("Z", C.c_void_p),
+                ("on_device", C.c_int32), ("preprojected", C.c_int32), ("inclination", C.c_double)]
+
+
+class RubixError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rubix status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "rubix_cube_create": (C.c_int32, [C.POINTER(rubix_ssp_grid), C.POINTER(rubix_telescope), C.c_int64,
+                                      C.POINTER(C.c_void_p)]),
+    "rubix_cube_forward": (C.c_int32, [C.c_void_p, C.POINTER(rubix_particles), C.c_uint64, C.c_float,
+                                       C.c_void_p, C.c_int32, C.c_void_p]),
+    "rubix_cube_backward": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rubix_cube_destroy": (C.c_int32, [C.c_void_p]),
+    "rubix_cube_spaxel_keys": (C.c_int32, [C.c_void_p, C.POINTER(rubix_particles), C.c_void_p, C.c_void_p]),
+    "rubix_cube_sorted": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rubix_cube_set_profiling": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "rubix_cube_stage_times": (C.c_int32, [C.c_void_p, _fp, C.POINTER(C.c_int32)]),
+    "rubix_cube_profile_history": (C.c_int32, [C.c_void_p, C.c_int32, _fp, C.POINTER(C.c_int32)]),
+    "rubix_cube_stats": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "rubix_last_error_message": (C.c_char_p, []),
+    "rubix_version": (C.c_char_p, []),
+}
+
+
+def load(path: str | None = None):
+    """Load librubix.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library not built: {p} is missing "
+                                   "(run paper_2412_08265_gb300.build.build())")
+            lib = C.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS.keys())
+
+
+def check(status: int):
+    if status != RUBIX_OK:
+        msg = load().rubix_last_error_message()
+        raise RubixError(status, msg.decode() if msg else "")
+    return status
+
+
+def _call(name, *args):
+    return check(getattr(load(), name)(*args))
+
+
+# ---------------------------------------------------------------------------
+# thin wrappers with the C names
+# ---------------------------------------------------------------------------
+def rubix_cube_create(ssp: rubix_ssp_grid, tel: rubix_telescope, max_particles: int) -> int:
+    h = C.c_void_p()
+    _call("rubix_cube_create", C.byref(ssp), C.byref(tel), C.c_int64(max_particles), C.byref(h))
+    return h.value
+
+
+def rubix_cube_forward(h: int, p: rubix_particles, noise_seed: int, noise_s2n: float, cube_out: int,
+                       cube_on_device: int, stream: int) -> None:
+    _call("rubix_cube_forward", C.c_void_p(h), C.byref(p), C.c_uint64(noise_seed), C.c_float(noise_s2n),
+          C.c_void_p(cube_out), C.c_int32(cube_on_device), C.c_void_p(stream))
+
+
+def rubix_cube_backward(h: int, dL_dcube: int, d_mass: int, d_age: int, d_Z: int, d_vlos: int,
+                        d_global: int, stream: int) -> None:
+    _call("rubix_cube_backward", C.c_void_p(h), C.c_void_p(dL_dcube), C.c_void_p(d_mass),
+          C.c_void_p(d_age), C.c_void_p(d_Z), C.c_void_p(d_vlos), C.c_void_p(d_global),
+          C.c_void_p(stream))
+
+
+def rubix_cube_destroy(h: int) -> None:
+    _call("rubix_cube_destroy", C.c_void_p(h))
+
+
+def rubix_cube_spaxel_keys(h: int, p: rubix_particles, keys_out: int, stream: int) -> None:
+    _call("rubix_cube_spaxel_keys", C.c_void_p(h), C.byref(p), C.c_void_p(keys_out), C.c_void_p(stream))
+
+
+def rubix_cube_sorted(h: int, perm_out: int, seg_off_out: int, stream: int) -> None:
+    _call("rubix_cube_sorted", C.c_void_p(h), C.c_void_p(perm_out), C.c_void_p(seg_off_out),
+          C.c_void_p(stream))
+
+
+def rubix_cube_set_profiling(h: int, enable: bool) -> None:
+    _call("rubix_cube_set_profiling", C.c_void_p(h), C.c_int32(1 if enable else 0))
+
+
+def rubix_cube_stage_times(h: int) -> list[float]:
+    buf = (C.c_float * 8)()
+    n = C.c_int32(8)
+    _call("rubix_cube_stage_times", C.c_void_p(h), buf, C.byref(n))
+    return [float(buf[i]) for i in range(n.value)]
+
+
+def rubix_cube_profile_history(h: int, stage: int) -> list[float]:
+    buf = (C.c_float * 256)()
+    n = C.c_int32(256)
+    _call("rubix_cube_profile_history", C.c_void_p(h), C.c_int32(stage), buf, C.byref(n))
+    return [float(buf[i]) for i in range(n.value)]
+
+
+def rubix_cube_stats(h: int) -> list[int]:
+    buf = (C.c_int64 * 8)()
+    n = C.c_int32(8)
+    _call("rubix_cube_stats", C.c_void_p(h), buf, C.byref(n))
+    return [int(buf[i]) for i in range(n.value)]
+
+
+def rubix_version() -> str:
+    return load().rubix_version().decode()

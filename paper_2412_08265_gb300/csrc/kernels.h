@@ -1,0 +1,135 @@
+// kernels.h -- internal launch interface between the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace rubix {
+
+struct DepRec;
+struct PartRec;
+struct Item;
+
+// K1 parameters.
+struct AssignParams {
+    long long n;
+    const float *x, *y, *z, *vy, *vz, *v_los;
+    int preprojected;
+    double cos_i, sin_i;
+    double x_lo, y_lo, inv_size;
+    int nx, ny;
+    int* key;         // [n]
+    double* v_out;    // [n] line-of-sight velocity (nullable)
+};
+
+int launch_assign(const AssignParams& P, cudaStream_t st);
+size_t scan_scratch_ints(long long n);
+int launch_exclusive_scan(const int* in, int* out, long long n, int* scratch, cudaStream_t st);
+size_t sort_scratch_ints(long long n);
+// Stable sort of keys in [0, n_keys); seg_off gets n_keys + 1 entries.
+int launch_sort_by_key(const int* keys, long long n, int n_keys, int* keys_tmp, int* vals_tmp, int* keys_out,
+                       int* perm_out, int* seg_off, int* scratch, cudaStream_t st);
+
+// SSP grid as stored on the device.
+struct SspDev {
+    const void* tpl;        // [n_t][pitch] in the storage dtype
+    int dtype;              // 0 f32, 1 bf16, 2 f16
+    int n_age, n_Z, n_t, n_ls, pitch;
+    const float* la_nodes;  // [n_age]
+    const float* lz_nodes;  // [n_Z]
+    double ls0, dls;
+};
+
+// K3: per-particle setup in sorted order + work items.
+struct SetupParams {
+    SspDev ssp;
+    const int* perm;         // sorted position -> particle index
+    const int* seg_off;      // [n_s + 2]
+    int n_s;
+    const float *mass, *age, *Z;
+    const double* v;         // line-of-sight velocity per particle
+    double l0, dl, z_cosmo, flux_scale;
+    int n_lambda;
+    DepRec* rec;             // [n_in]
+    PartRec* prec;           // [n_in]
+    long long n_cap;         // capacity of rec / prec
+};
+int launch_setup(const SetupParams& P, long long n_total, cudaStream_t st);
+
+struct ItemParams {
+    const int* seg_off;      // [n_s + 2]
+    int n_s;
+    int chunk;               // max particles per item
+    int* n_items;            // [n_s + 1] scratch
+    int* n_parts;            // [n_s + 1] scratch
+    int* item_off;           // [n_s + 1]
+    int* part_off;           // [n_s + 1]
+    Item* items;             // capacity item_cap
+    long long item_cap;
+    int* scan_scratch;
+    unsigned* err;
+};
+int launch_items(const ItemParams& P, cudaStream_t st);
+
+// K4: deposit.
+struct DepositParams {
+    SspDev ssp;
+    const DepRec* rec;
+    const Item* items;
+    const int* item_off;     // [n_s + 1]: total items at [n_s]
+    const int* seg_off;      // [n_s + 2]: in-field particles at [n_s]
+    int n_s;
+    int n_lambda;
+    int tile_w;              // output bins per tile, multiple of 32
+    int n_tiles;
+    const int* tile_klo;     // [n_tiles] first SSP node of each tile's slab
+    int slab_w;              // nodes per slab row (0 = no slab: global path only)
+    int box_rows, n_boxes;   // TMA boxes covering the template rows
+    int cost_c0;             // per-item cost in particle units
+    float* cube;             // [n_s][n_lambda]
+    float* partials;         // [n_parts][n_lambda]
+    long long part_cap;      // rows of `partials`
+    unsigned* err;
+    unsigned long long* slow_count;
+};
+int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,
+                   cudaStream_t st);
+size_t deposit_smem_bytes(int n_rows_alloc, int slab_w, int elem_bytes);
+
+// K5: combine partial rows of split spaxels in FP64, fixed order.
+int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube,
+                   cudaStream_t st);
+
+// K6: PSF + LSF (+ noise).
+constexpr int kMaxRadius = 64;
+struct ConvParams {
+    int nx, ny, n_lambda;
+    int rp, rl;                  // radii (0 = identity)
+    float gp[2 * kMaxRadius + 1];
+    float gl[2 * kMaxRadius + 1];
+    float noise_inv_s2n;         // 0 = no noise
+    uint32_t seed_lo, seed_hi;
+};
+int launch_psf_lsf(const ConvParams& P, const float* in, float* tmp, float* out, cudaStream_t st);
+
+// K7/K8: adjoint.
+struct AdjointParams {
+    SspDev ssp;
+    const PartRec* prec;       // [n_in] sorted order
+    const int* perm;           // sorted position -> particle index
+    const int* seg_off;        // [n_s + 2]
+    const int* sorted_keys;    // [n] key per sorted position
+    int n_s, n_lambda;
+    double l0, dl, z_cosmo, flux_scale;
+    const float* G0;           // [n_s][n_lambda] dL/dcube0
+    float *d_mass, *d_age, *d_Z, *d_v;   // original order, nullable
+    double* contrib;           // [n_in][2] per sorted particle: dL/dv, m*dL/dm (FP64)
+    long long n_in;
+};
+int launch_adjoint_rec(const AdjointParams& P, const DepRec* rec, cudaStream_t st);
+int launch_zero_grads(float* a, float* b, float* c, float* d, long long n, cudaStream_t st);
+int launch_reduce_global(const double* contrib, const int* n_in_dev, double* out2, double* scratch, cudaStream_t st);
+
+}  // namespace rubix

@@ -1,0 +1,285 @@
+// sort.cu -- orientation + spaxel keys (Sec. 3: "orientate the galaxy",
+// "particles are assigned to the IFU spaxels") and the deterministic stable
+// sort of particles by spaxel that replaces global atomics in the per-spaxel
+// sum ("the stellar spectra in each spaxel are summed up").
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rubix {
+
+// ----------------------------------------------------------------------------
+// K1: orientation + spaxel key. Reading: x' = x, y' = y cos i - z sin i,
+// v = vy sin i + vz cos i; x_lo = (-0.5 nx) size; u = (x' - x_lo) * (1/size);
+// every FP64 op rounded once (explicit _rn intrinsics, no contraction), so the
+// integer key is bit-identical to a host evaluation of the same expression.
+// ----------------------------------------------------------------------------
+__global__ void k_assign(AssignParams P) {
+    const long long n = P.n;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        double xp, yp, v;
+        if (P.preprojected) {
+            xp = (double)P.x[p];
+            yp = (double)P.y[p];
+            v = P.v_los ? (double)P.v_los[p] : 0.0;
+        } else {
+            double a = __dmul_rn((double)P.y[p], P.cos_i);
+            double b = __dmul_rn((double)P.z[p], P.sin_i);
+            xp = (double)P.x[p];
+            yp = __dsub_rn(a, b);
+            if (P.vy) {
+                double c = __dmul_rn((double)P.vy[p], P.sin_i);
+                double d = __dmul_rn((double)P.vz[p], P.cos_i);
+                v = __dadd_rn(c, d);
+            } else {
+                v = 0.0;
+            }
+        }
+        double u = __dmul_rn(__dsub_rn(xp, P.x_lo), P.inv_size);
+        double w = __dmul_rn(__dsub_rn(yp, P.y_lo), P.inv_size);
+        int key;
+        if (u >= 0.0 && u < (double)P.nx && w >= 0.0 && w < (double)P.ny)
+            key = (int)w * P.nx + (int)u;
+        else
+            key = P.nx * P.ny;
+        P.key[p] = key;
+        if (P.v_out) P.v_out[p] = v;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Exclusive scan of int32 (3 phases: block sums, scan of sums, block scans).
+// ----------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
+        int s = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_tot[lane] = s - t;
+        if (lane == 31) *total = s;
+    }
+    __syncthreads();
+    int r = x - v + warp_tot[wid];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const int* __restrict__ in, long long n, int* __restrict__ sums) {
+    __shared__ int wt[32];
+    __shared__ int tot;
+    long long base = (long long)blockIdx.x * kScanTile;
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        long long idx = base + (long long)i * kScanThreads + threadIdx.x;
+        if (idx < n) s += in[idx];
+    }
+    block_exclusive_scan(s, wt, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int* sums, int nb) {
+    __shared__ int wt[32];
+    __shared__ int tot;
+    int carry = 0;
+    for (int base = 0; base < nb; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = (i < nb) ? sums[i] : 0;
+        int e = block_exclusive_scan(v, wt, &tot);
+        if (i < nb) sums[i] = carry + e;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_apply(const int* __restrict__ in, long long n, const int* __restrict__ sums,
+                             int* __restrict__ out) {
+    __shared__ int wt[32];
+    __shared__ int tot;
+    long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        long long idx = base + i;
+        v[i] = (idx < n) ? in[idx] : 0;
+        s += v[i];
+    }
+    int e = block_exclusive_scan(s, wt, &tot) + sums[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        long long idx = base + i;
+        if (idx < n) out[idx] = e;
+        e += v[i];
+    }
+}
+
+size_t scan_scratch_ints(long long n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
+
+int launch_exclusive_scan(const int* in, int* out, long long n, int* scratch, cudaStream_t st) {
+    if (n <= 0) return 0;
+    int nb = (int)((n + kScanTile - 1) / kScanTile);
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, scratch);
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(scratch, nb);
+    k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, n, scratch, out);
+    return 3;
+}
+
+// ----------------------------------------------------------------------------
+// Stable LSD radix sort of (key, particle index), up to 9 bits per pass.
+// Per pass: per-tile digit counts (digit-major), exclusive scan, then a stable
+// scatter in which each warp ranks its keys in index order with match.any.
+// ----------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys
+constexpr int kMaxBuckets = 512;
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int* __restrict__ keys, long long n, int shift,
+                                                             int nbits, int n_tiles, int* __restrict__ counts) {
+    __shared__ int hist[kMaxBuckets];
+    const int nb = 1 << nbits, mask = nb - 1;
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) hist[d] = 0;
+    __syncthreads();
+    long long base = (long long)blockIdx.x * kSortTile;
+    for (int i = threadIdx.x; i < kSortTile; i += blockDim.x) {
+        long long idx = base + i;
+        if (idx < n) atomicAdd(&hist[(keys[idx] >> shift) & mask], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) counts[(long long)d * n_tiles + blockIdx.x] = hist[d];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const int* __restrict__ keys_in,
+                                                                const int* __restrict__ vals_in, long long n,
+                                                                int shift, int nbits, int n_tiles,
+                                                                const int* __restrict__ offsets,
+                                                                int* __restrict__ keys_out,
+                                                                int* __restrict__ vals_out) {
+    __shared__ int wcnt[kSortWarps][kMaxBuckets];
+    const int nb = 1 << nbits, mask = nb - 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < nb; d += 32) wcnt[w][d] = 0;
+    __syncwarp();
+    const long long base = (long long)blockIdx.x * kSortTile + (long long)w * (kSortTile / kSortWarps);
+    const unsigned lt = (1u << lane) - 1u;
+    int key[kSortRounds], rank[kSortRounds];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        long long idx = base + r * 32 + lane;
+        bool valid = idx < n;
+        int k = valid ? keys_in[idx] : 0;
+        int d = valid ? ((k >> shift) & mask) : (nb + 1);
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = valid ? wcnt[w][d] : 0;
+        __syncwarp();
+        int leader = 31 - __clz(peers);
+        if (valid && lane == leader) wcnt[w][d] = before + __popc(peers);
+        __syncwarp();
+        key[r] = k;
+        rank[r] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) {
+        int run = 0;
+#pragma unroll
+        for (int ww = 0; ww < kSortWarps; ++ww) {
+            int t = wcnt[ww][d];
+            wcnt[ww][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        long long idx = base + r * 32 + lane;
+        if (idx < n) {
+            int d = (key[r] >> shift) & mask;
+            long long pos = (long long)offsets[(long long)d * n_tiles + blockIdx.x] + wcnt[w][d] + rank[r];
+            keys_out[pos] = key[r];
+            vals_out[pos] = vals_in ? vals_in[idx] : (int)idx;
+        }
+    }
+}
+
+// seg_off[s] = first sorted position with key >= s, for s in [0, n_keys]; the
+// sorted keys are in [0, n_keys).
+__global__ void k_seg_bounds(const int* __restrict__ skeys, long long n, int n_keys, int* __restrict__ seg_off) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= n;
+         i += (long long)gridDim.x * blockDim.x) {
+        int prev = (i == 0) ? -1 : skeys[i - 1];
+        int cur = (i == n) ? n_keys : skeys[i];
+        for (int s = prev + 1; s <= cur; ++s) seg_off[s] = (int)i;
+    }
+}
+
+size_t sort_scratch_ints(long long n) {
+    long long n_tiles = (n + kSortTile - 1) / kSortTile;
+    long long counts = n_tiles * kMaxBuckets;
+    return (size_t)(2 * counts) + scan_scratch_ints(counts) + 16;
+}
+
+int launch_sort_by_key(const int* keys, long long n, int n_keys, int* keys_tmp, int* vals_tmp, int* keys_out,
+                       int* perm_out, int* seg_off, int* scratch, cudaStream_t st) {
+    int launches = 0;
+    if (n > 0) {
+        int bits = 1;
+        while ((1ll << bits) < (long long)n_keys) ++bits;   // keys lie in [0, n_keys)
+        int passes = (bits + 8) / 9;
+        int per = (bits + passes - 1) / passes;
+        int n_tiles = (int)((n + kSortTile - 1) / kSortTile);
+        long long n_counts = (long long)n_tiles << per;
+        int* counts = scratch;
+        int* offs = scratch + n_counts;
+        int* sscr = offs + n_counts;
+        const int* kin = keys;
+        const int* vin = nullptr;
+        for (int ps = 0; ps < passes; ++ps) {
+            int shift = ps * per;
+            int nb = (ps == passes - 1) ? (bits - shift) : per;
+            // ping-pong so that the last pass lands in keys_out / perm_out
+            bool to_final = ((passes - 1 - ps) % 2) == 0;
+            int* kout = to_final ? keys_out : keys_tmp;
+            int* vout = to_final ? perm_out : vals_tmp;
+            long long cnt = (long long)n_tiles << nb;
+            k_radix_hist<<<n_tiles, kSortThreads, 0, st>>>(kin, n, shift, nb, n_tiles, counts);
+            launches += 1 + launch_exclusive_scan(counts, offs, cnt, sscr, st);
+            k_radix_scatter<<<n_tiles, kSortThreads, 0, st>>>(kin, vin, n, shift, nb, n_tiles, offs, kout, vout);
+            ++launches;
+            kin = kout;
+            vin = vout;
+        }
+    }
+    int nt = (int)((n + 1 + 255) / 256);
+    if (nt > 4096) nt = 4096;
+    k_seg_bounds<<<nt, 256, 0, st>>>(keys_out, n, n_keys, seg_off);
+    return launches + 1;
+}
+
+int launch_assign(const AssignParams& P, cudaStream_t st) {
+    if (P.n <= 0) return 0;
+    long long nb = (P.n + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    k_assign<<<(int)nb, 256, 0, st>>>(P);
+    return 1;
+}
+
+}  // namespace rubix

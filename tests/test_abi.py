@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/rubix.h (no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(rubix_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2412_08265_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("rubix_cube_create", "rubix_cube_forward", "rubix_cube_backward", "rubix_cube_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    missing = [n for n in declared_symbols() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_matches(lib_path):
+    from paper_2412_08265_gb300 import capi
+    lib = capi.load()
+    assert capi.rubix_version().startswith("rubix-gb300")
+    for n in declared_symbols():
+        assert hasattr(lib, n)
+    assert set(capi.exported_symbols()) <= set(declared_symbols())
+
+
+def test_invalid_arguments_are_reported_without_a_gpu(lib_path):
+    """Argument validation happens on the host before any CUDA call."""
+    from paper_2412_08265_gb300 import capi
+    capi.load()
+    h = ctypes.c_void_p()
+    rc = capi.load().rubix_cube_create(None, None, 0, ctypes.byref(h))
+    assert rc == capi.RUBIX_ERR_INVALID_ARG and h.value is None
+    assert b"NULL" in capi.load().rubix_last_error_message()
+

@@ -1,0 +1,310 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer work (spaxel keys, sort order, segment offsets) must be bit-exact.
+Cubes must satisfy max|GPU - oracle| / max|oracle| <= 1e-5 with FP32
+templates and <= 2e-3 with BF16 templates (the error bound of the forward
+model's stated precision); each test states its tolerance.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_08265_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_BF16 = 2e-3
+NT = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from __graft_entry__ import build
+    build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def make_model(wl_or_ssp, tel=None, dtype="f32", n=1 << 16):
+    from paper_2412_08265_gb300.model import CubeModel
+    if tel is None:
+        return CubeModel(wl_or_ssp.ssp, wl_or_ssp.telescope, dtype, max_particles=n)
+    return CubeModel(wl_or_ssp, tel, dtype, max_particles=n)
+
+
+def rel_err(got, ref):
+    return float(np.abs(got.astype(np.float64) - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def bf16_round(a):
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def edge_particles(tel, n_extra=64, seed=9):
+    """Particles exactly on spaxel edges, on the field border and outside it."""
+    rng = np.random.default_rng(seed)
+    size = tel.spaxel_size
+    xl = -0.5 * tel.nx * size
+    yl = -0.5 * tel.ny * size
+    ix = rng.integers(0, tel.nx + 1, n_extra)
+    iy = rng.integers(0, tel.ny + 1, n_extra)
+    x = (xl + ix * size).astype(np.float32)
+    y = (yl + iy * size).astype(np.float32)
+    x[:4] = [xl, -xl, np.float32(xl) - np.float32(1e-6), 0.0]
+    y[:4] = [yl, 0.0, 0.0, -yl]
+    f = lambda a: np.asarray(a, dtype=np.float32)
+    return synth.Particles(x=x, y=y, mass=f(np.full(n_extra, 1e5)), age=f(np.full(n_extra, 1.0)),
+                           Z=f(np.full(n_extra, 0.01)), v_los=f(np.zeros(n_extra)), preprojected=True)
+
+
+def concat(a, b):
+    cat = lambda u, v: None if u is None else np.concatenate([u, v])
+    return synth.Particles(x=cat(a.x, b.x), y=cat(a.y, b.y), mass=cat(a.mass, b.mass), age=cat(a.age, b.age),
+                           Z=cat(a.Z, b.Z), v_los=cat(a.v_los, b.v_los), preprojected=True)
+
+
+# ---------------------------------------------------------------------------
+# a1/a2 keys and a3 sort: bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["small", "mid", "inclined"])
+def test_spaxel_keys_bit_exact(torch_cuda, kind):
+    if kind == "small":
+        wl = synth.small_galaxy()
+        p = concat(wl.particles, edge_particles(wl.telescope))
+        tel = wl.telescope
+    elif kind == "mid":
+        wl = synth.mid_galaxy(n=200_000)
+        p = concat(wl.particles, edge_particles(wl.telescope, 512))
+        tel = wl.telescope
+    else:
+        wl = synth.small_galaxy()
+        tel = synth.serving_telescope(73)
+        p = synth.disk_3d(50_000, 21, inclination=0.83)
+    model = make_model(wl.ssp, tel, n=p.n)
+    got = model.spaxel_keys(p).cpu().numpy()
+    xp, yp, _ = oracle.orient(p)
+    ref = oracle.spaxel_keys(xp, yp, tel)
+    assert np.array_equal(got, ref), np.flatnonzero(got != ref)[:10]
+    model.close()
+
+
+def test_sort_and_segments_bit_exact(torch_cuda):
+    wl = synth.mid_galaxy(n=300_000)
+    model = make_model(wl, n=wl.particles.n)
+    model.forward(wl.particles)
+    perm, seg = model.sorted()
+    xp, yp, _ = oracle.orient(wl.particles)
+    key = oracle.spaxel_keys(xp, yp, wl.telescope)
+    n_s = wl.telescope.nx * wl.telescope.ny
+    operm, oseg = oracle.stable_sort(key, n_s + 1)
+    assert np.array_equal(perm.cpu().numpy(), operm)
+    assert np.array_equal(seg.cpu().numpy().astype(np.int64), oseg)
+    model.close()
+
+
+# ---------------------------------------------------------------------------
+# forward cube parity
+# ---------------------------------------------------------------------------
+def test_forward_small_galaxy(torch_cuda):
+    wl = synth.small_galaxy()
+    model = make_model(wl, n=wl.particles.n)
+    got = model.forward(wl.particles).cpu().numpy()
+    ref = oracle.forward(wl.particles, wl.ssp, wl.telescope, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_F32
+    st = model.stats()
+    assert st["device_error"] == 0 and st["slow_particle_tiles"] == 0
+    model.close()
+
+
+def test_forward_pre_convolution_and_each_kernel(torch_cuda):
+    """Deposit alone, PSF alone and LSF alone against the oracle."""
+    wl = synth.small_galaxy(n=5000, seed=3)
+    for fwhm, sig in ((0.0, 0.0), (1.5, 0.0), (0.0, 1.2), (2.5, 4.0)):
+        tel = synth.Telescope(**{**wl.telescope.__dict__, "psf_fwhm": fwhm, "lsf_sigma": sig})
+        model = make_model(wl.ssp, tel, n=wl.particles.n)
+        got = model.forward(wl.particles).cpu().numpy()
+        ref = oracle.forward(wl.particles, wl.ssp, tel, n_threads=NT)
+        assert rel_err(got, ref) <= TOL_F32, (fwhm, sig)
+        model.close()
+
+
+def test_forward_many_tiles_ragged_tail(torch_cuda):
+    """n_lambda not a multiple of the tile width, several tiles, odd field."""
+    ssp = synth.ssp_grid(7, 5, 900, 4700.0, 6500.0, seed=5)
+    tel = synth.Telescope(nx=13, ny=9, spaxel_size=0.7, n_lambda=1237, lambda0=4760.0, dlambda=1.3,
+                          psf_fwhm=1.7, lsf_sigma=1.9)
+    p = synth.disk_projected(20_000, 8)
+    model = make_model(ssp, tel, n=p.n)
+    got = model.forward(p).cpu().numpy()
+    ref = oracle.forward(p, ssp, tel, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_F32
+    assert model.stats()["device_error"] == 0
+    model.close()
+
+
+def test_forward_mid_galaxy_sampled_spaxels(torch_cuda):
+    """Full mid-size workload (1e6 particles, 150x150x3721, FP32 templates) in the
+    bench's launch configuration; the oracle evaluates sampled spaxels exactly."""
+    wl = synth.mid_galaxy()
+    tel = wl.telescope
+    model = make_model(wl, n=wl.particles.n)
+    got = model.forward(wl.particles).cpu().numpy()
+    parts_key = oracle.spaxel_keys(*oracle.orient(wl.particles)[:2], tel)
+    counts = np.bincount(parts_key, minlength=tel.nx * tel.ny + 1)[:-1]
+    rng = np.random.default_rng(17)
+    heavy = np.argsort(counts)[-3:]                   # densest spaxels (split items)
+    rand = rng.choice(np.flatnonzero(counts > 0), 5, replace=False)
+    edge = np.array([0, tel.nx - 1, tel.nx * tel.ny - 1])
+    sel = np.unique(np.concatenate([heavy, rand, edge])).astype(np.int32)
+    mask = np.zeros(tel.nx * tel.ny, np.uint8)
+    r = 3
+    for s in sel:
+        y, x = divmod(int(s), tel.nx)
+        for yy in range(max(0, y - r), min(tel.ny, y + r + 1)):
+            mask[yy * tel.nx + max(0, x - r): yy * tel.nx + min(tel.nx, x + r + 1)] = 1
+    xp, yp, v = oracle.orient(wl.particles)
+    cube0 = oracle.deposit(parts_key, v, wl.particles, wl.ssp, tel, mask=mask, n_threads=NT)
+    ref = oracle.psf_lsf_at(cube0, tel, sel)
+    g = got.reshape(-1, tel.n_lambda)[sel]
+    # scale: the global maximum of the cube (the densest spaxel is in `sel`)
+    scale = float(np.abs(ref).max())
+    assert float(np.abs(g - ref).max()) / scale <= TOL_F32
+    # property at full size: total flux equals the sum of all deposits minus edge losses
+    assert np.isfinite(got).all() and got.min() >= 0.0
+    st = model.stats()
+    assert st["device_error"] == 0
+    assert st["n_in_fov"] == int(counts.sum())
+    model.close()
+
+
+def test_deterministic_bitwise(torch_cuda):
+    wl = synth.mid_galaxy(n=200_000)
+    model = make_model(wl, n=wl.particles.n)
+    a = model.forward(wl.particles).cpu().numpy()
+    b = model.forward(wl.particles).cpu().numpy()
+    assert np.array_equal(a, b)
+    model.close()
+
+
+def test_empty_outside_and_single(torch_cuda):
+    wl = synth.small_galaxy(n=10)
+    model = make_model(wl, n=16)
+    f = lambda a: np.asarray(a, dtype=np.float32)
+    empty = synth.Particles(x=f([]), y=f([]), mass=f([]), age=f([]), Z=f([]), v_los=f([]))
+    assert not model.forward(empty).cpu().numpy().any()
+    outside = synth.Particles(x=f([100.0, -50.0]), y=f([0.0, 3.0]), mass=f([1e5, 1e5]), age=f([1, 2]),
+                              Z=f([0.01, 0.02]), v_los=f([0, 0]))
+    assert not model.forward(outside).cpu().numpy().any()
+    one = synth.Particles(x=f([0.3]), y=f([-1.1]), mass=f([2e5]), age=f([3.3]), Z=f([0.004]), v_los=f([123.0]))
+    got = model.forward(one).cpu().numpy()
+    ref = oracle.forward(one, wl.ssp, wl.telescope, n_threads=1)
+    assert rel_err(got, ref) <= TOL_F32
+    model.close()
+
+
+def test_heavy_spaxel_split_fp64_combine(torch_cuda):
+    """> chunk particles in a single spaxel: split items combined in FP64."""
+    wl = synth.small_galaxy()
+    rng = np.random.default_rng(4)
+    n = 5000
+    f = lambda a: np.asarray(a, dtype=np.float32)
+    p = synth.Particles(x=f(rng.uniform(0.01, 0.49, n)), y=f(rng.uniform(0.01, 0.49, n)),
+                        mass=f(np.exp(rng.normal(np.log(1e5), 0.5, n))),
+                        age=f(np.exp(rng.uniform(np.log(0.1), np.log(13.5), n))),
+                        Z=f(np.exp(rng.uniform(np.log(1e-4), np.log(0.04), n))),
+                        v_los=f(rng.normal(0, 80, n)))
+    model = make_model(wl, n=n)
+    got = model.forward(p).cpu().numpy()
+    ref = oracle.forward(p, wl.ssp, wl.telescope, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_F32
+    model.close()
+
+
+def test_high_velocity_slow_path(torch_cuda):
+    """Particles beyond the shared-memory Doppler halo take the global path."""
+    wl = synth.mid_galaxy(n=20_000)
+    p = wl.particles
+    p.v_los = p.v_los.copy()
+    p.v_los[::7] = np.float32(4000.0)
+    p.v_los[3::7] = np.float32(-3500.0)
+    tel = synth.Telescope(nx=40, ny=40, spaxel_size=0.5, n_lambda=3721, lambda0=4750.0, dlambda=1.25)
+    model = make_model(wl.ssp, tel, n=p.n)
+    got = model.forward(p).cpu().numpy()
+    ref = oracle.forward(p, wl.ssp, tel, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_F32
+    assert model.stats()["slow_particle_tiles"] > 0
+    model.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_reduced_precision_templates(torch_cuda, dtype):
+    wl = synth.small_galaxy(n=20_000, seed=6)
+    model = make_model(wl.ssp, wl.telescope, dtype=dtype, n=wl.particles.n)
+    got = model.forward(wl.particles).cpu().numpy()
+    ref = oracle.forward(wl.particles, wl.ssp, wl.telescope, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_BF16
+    assert abs(got.sum() / ref.sum() - 1.0) <= TOL_BF16
+    if dtype == "bf16":
+        refq = oracle.forward(wl.particles, wl.ssp, wl.telescope, n_threads=NT, spectra=bf16_round(wl.ssp.spectra))
+    else:
+        refq = oracle.forward(wl.particles, wl.ssp, wl.telescope, n_threads=NT,
+                              spectra=wl.ssp.spectra.astype(np.float32).astype(np.float16).astype(np.float64))
+    assert rel_err(got, refq) <= TOL_F32
+    model.close()
+
+
+def test_inclined_3d_galaxy(torch_cuda):
+    wl = synth.small_galaxy()
+    tel = synth.Telescope(nx=48, ny=40, spaxel_size=0.3, n_lambda=700, lambda0=4050.0, dlambda=3.0)
+    p = synth.disk_3d(30_000, 31, inclination=1.2)
+    model = make_model(wl.ssp, tel, n=p.n)
+    got = model.forward(p).cpu().numpy()
+    ref = oracle.forward(p, wl.ssp, tel, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_F32
+    model.close()
+
+
+def test_host_buffers_end_to_end(torch_cuda):
+    """Host particle arrays in, host cube out, through the C ABI."""
+    import ctypes as C
+    from paper_2412_08265_gb300 import capi
+    wl = synth.small_galaxy(n=3000, seed=2)
+    model = make_model(wl, n=wl.particles.n)
+    p = wl.particles
+    arrs = {k: np.ascontiguousarray(getattr(p, k), dtype=np.float32) for k in ("x", "y", "v_los", "mass", "age", "Z")}
+    cp = model.c_particles({**arrs, "preprojected": True, "inclination": 0.0}, on_device=False)
+    out = np.empty(model.cube_shape, dtype=np.float32)
+    capi.rubix_cube_forward(model.handle, cp, 0, 0.0, out.ctypes.data, 0, 0)
+    ref = oracle.forward(p, wl.ssp, wl.telescope, n_threads=NT)
+    assert rel_err(out, ref) <= TOL_F32
+    model.close()
+
+
+def test_noise_statistics_and_reproducibility(torch_cuda):
+    """Noise is Gaussian with sigma = |cube|/S2N: z-scores have mean 0, variance 1
+    and pass a KS test; the same seed reproduces bitwise, another seed differs."""
+    from scipy import stats
+    wl = synth.small_galaxy()
+    model = make_model(wl, n=wl.particles.n)
+    clean = oracle.forward(wl.particles, wl.ssp, wl.telescope, n_threads=NT)
+    a = model.forward(wl.particles, noise_seed=777, noise_s2n=30.0).cpu().numpy()
+    b = model.forward(wl.particles, noise_seed=777, noise_s2n=30.0).cpu().numpy()
+    c = model.forward(wl.particles, noise_seed=778, noise_s2n=30.0).cpu().numpy()
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    sig = np.abs(clean) / 30.0
+    m = sig > 1e-6 * np.abs(clean).max()
+    z = ((a.astype(np.float64) - clean)[m] / sig[m])
+    n = z.size
+    assert n > 100_000
+    assert abs(z.mean()) < 5 / math.sqrt(n)
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / n)
+    assert stats.kstest(z[:200_000], "norm").pvalue > 1e-3
+    model.close()
