@@ -164,7 +164,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2412_08265_gb300 import synth
-    wl = synth.mid_galaxy()
+    wl = synth.mid_galaxy(n=args.particles)
     times, deps = [], []
     per_step = max(3.0, 60.0 / max(args.steps + args.warmup, 1))
     for i in range(args.warmup + args.steps):
@@ -204,7 +204,7 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    wl = synth.mid_galaxy(seed=1 + rank)
+    wl = synth.mid_galaxy(n=args.particles, seed=1 + rank)
     model = CubeModel(wl.ssp, wl.telescope, "f32", max_particles=wl.particles.n, device=dev)
     d = model.device_particles(wl.particles)
     out = torch.empty(model.cube_shape, dtype=torch.float32, device=dev)
@@ -325,6 +325,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--particles", type=int, default=1_000_000,
+                    help="particles of the mid-size galaxy (smaller only for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
