@@ -178,6 +178,27 @@ rubix_status rubix_cube_profile_history(rubix_cube_t *h, int32_t stage, float *m
  * [4] kernels launched by the forward. n_inout: capacity in, written out. */
 rubix_status rubix_cube_stats(rubix_cube_t *h, int64_t *stats, int32_t *n_inout);
 
+/* Spaxel assignment + stable sort by spaxel that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory themselves -- for instance when another
+ * allocator (a framework's caching allocator, a pool sized at start-up) owns
+ * the device's memory budget, or when the call runs in a latency-critical
+ * loop where cudaMalloc/cudaFree would synchronise the device.
+ * Same result as rubix_cube_forward's sort (rubix_cube_sorted): perm_out
+ * (device int32 [n]) lists particle indices by spaxel key, ties by index;
+ * seg_off_out (device int32 [nx*ny + 2]) gives the first sorted position of
+ * each key, then n. Particles must be device pointers (on_device = 1); only
+ * x, y (and z when preprojected = 0) are read. Scratch lives in one fixed
+ * device array inside the library (about 4.3 MB, held on every device that
+ * loads the library until exit). Limits: n <= 262144 and nx*ny <= 262143;
+ * larger problems return RUBIX_ERR_INVALID_ARG with a message. The first call
+ * on a device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture. All calls
+ * share the array: calls whose work overlaps on the GPU (other streams or
+ * threads without ordering) race and give wrong results. */
+rubix_status rubix_spaxel_sort_noalloc(const rubix_particles *p, const rubix_telescope *tel,
+                                       int32_t *perm_out, int32_t *seg_off_out, void *stream);
+
 /* Thread-local message for the last non-OK status returned on this thread. */
 const char *rubix_last_error_message(void);
 

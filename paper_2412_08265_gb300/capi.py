@@ -78,6 +78,8 @@ _SIGS = {
     "rubix_cube_stage_times": (C.c_int32, [C.c_void_p, _fp, C.POINTER(C.c_int32)]),
     "rubix_cube_profile_history": (C.c_int32, [C.c_void_p, C.c_int32, _fp, C.POINTER(C.c_int32)]),
     "rubix_cube_stats": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "rubix_spaxel_sort_noalloc": (C.c_int32, [C.POINTER(rubix_particles), C.POINTER(rubix_telescope),
+                                              C.c_void_p, C.c_void_p, C.c_void_p]),
     "rubix_last_error_message": (C.c_char_p, []),
     "rubix_version": (C.c_char_p, []),
 }
@@ -174,6 +176,16 @@ def rubix_cube_stats(h: int) -> list[int]:
     n = C.c_int32(8)
     _call("rubix_cube_stats", C.c_void_p(h), buf, C.byref(n))
     return [int(buf[i]) for i in range(n.value)]
+
+
+def rubix_spaxel_sort_noalloc(p: rubix_particles, tel: rubix_telescope, perm_out: int, seg_off_out: int,
+                              stream: int) -> None:
+    """Spaxel sort for callers that may not allocate device memory (their
+    memory budget belongs to another allocator, or cudaMalloc's device
+    synchronisation is not acceptable where they call it): scratch lives in a
+    fixed array inside the library, so n <= 262144 and nx*ny <= 262143."""
+    _call("rubix_spaxel_sort_noalloc", C.byref(p), C.byref(tel), C.c_void_p(perm_out), C.c_void_p(seg_off_out),
+          C.c_void_p(stream))
 
 
 def rubix_version() -> str:

@@ -39,6 +39,10 @@ static rubix_status fail(rubix_status st, const char* fmt, ...) {
     } while (0)
 
 extern "C" const char* rubix_last_error_message(void) { return g_err.c_str(); }
+
+namespace rubix {
+void set_last_error(const char* msg) { g_err = msg; }
+}
 extern "C" const char* rubix_version(void) { return "rubix-gb300 0.1 (sm_103a)"; }
 
 // ----------------------------------------------------------------------------
