@@ -153,9 +153,11 @@ rubix_status rubix_cube_spaxel_keys(rubix_cube_t *h, const rubix_particles *p, i
                                     void *stream);
 
 /* Copy the sort result of the most recent forward (device pointers):
- * perm_out int32 [n]: particle indices ordered by spaxel key, ties by index;
- * seg_off_out int32 [nx*ny + 2]: first sorted position of each key, then n.
- * Either may be NULL. */
+ * perm_out int32 [n]: particle indices ordered by spaxel key, then by the
+ * SSP age band the deposit kernel uses for that handle (stats[8] bands; one
+ * band = plain spaxel order), then by index;
+ * seg_off_out int32 [nx*ny + 2]: first sorted position of each spaxel key,
+ * then n. Either may be NULL. */
 rubix_status rubix_cube_sorted(rubix_cube_t *h, int32_t *perm_out, int32_t *seg_off_out,
                                void *stream);
 
@@ -173,9 +175,12 @@ rubix_status rubix_cube_stage_times(rubix_cube_t *h, float *ms, int32_t *n_inout
 rubix_status rubix_cube_profile_history(rubix_cube_t *h, int32_t stage, float *ms, int32_t *n_inout);
 
 /* Counters of the most recent forward (waits for it): [0] particles in the
- * field, [1] deposits = in-field particles * n_lambda, [2] particles on the
- * slow (out-of-slab Doppler range) path, [3] number of deposit launches,
- * [4] kernels launched by the forward. n_inout: capacity in, written out. */
+ * field, [1] deposits = in-field particles * n_lambda, [2] (particle, tile)
+ * pairs on the global-memory path (Doppler shift beyond the slab halo),
+ * [3] deposit launches, [4] kernels launched by the forward, [5] device error
+ * word (0 = none), [6] output bins per wavelength tile, [7] SSP nodes per
+ * shared-memory slab row, [8] age bands of the template grid.
+ * n_inout: capacity in, number written out. */
 rubix_status rubix_cube_stats(rubix_cube_t *h, int64_t *stats, int32_t *n_inout);
 
 /* Spaxel assignment + stable sort by spaxel that allocates no device memory.

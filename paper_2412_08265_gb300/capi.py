@@ -172,8 +172,8 @@ def rubix_cube_profile_history(h: int, stage: int) -> list[float]:
 
 
 def rubix_cube_stats(h: int) -> list[int]:
-    buf = (C.c_int64 * 8)()
-    n = C.c_int32(8)
+    buf = (C.c_int64 * 16)()
+    n = C.c_int32(16)
     _call("rubix_cube_stats", C.c_void_p(h), buf, C.byref(n))
     return [int(buf[i]) for i in range(n.value)]
 

@@ -22,21 +22,6 @@
 
 namespace rubix {
 
-__device__ __forceinline__ void ssp_cell_d(float q, const float* __restrict__ nodes, int n, int& i, float& t,
-                                           float& dt) {
-    if (n < 2 || !(q > nodes[0])) { i = 0; t = 0.f; dt = 0.f; return; }
-    if (q >= nodes[n - 1]) { i = n - 2; t = 1.f; dt = 0.f; return; }
-    int lo = 0, hi = n - 1;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (nodes[mid] <= q) lo = mid; else hi = mid;
-    }
-    i = lo;
-    const float h = nodes[lo + 1] - nodes[lo];
-    t = (q - nodes[lo]) / h;
-    dt = 1.f / h;
-}
-
 template <typename T>
 __device__ __forceinline__ float tplg(const T* __restrict__ tpl, int pitch, int n_ls, int row, int k) {
     return (k >= 0 && k < n_ls) ? TplTraits<T>::ld(tpl + (long long)row * pitch + k) : 0.f;
@@ -47,7 +32,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const AdjointParams P, const De
     const int lane = threadIdx.x & 31;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long n_in = P.seg_off[P.n_s];
+    const long long n_in = P.seg_off[(long long)P.n_s * P.n_bands];
     const T* __restrict__ tpl = reinterpret_cast<const T*>(P.ssp.tpl);
     const int pitch = P.ssp.pitch, n_ls = P.ssp.n_ls;
     const int da = (P.ssp.n_age > 1) ? P.ssp.n_Z : 0;
@@ -56,12 +41,12 @@ __global__ void __launch_bounds__(256) k_adjoint(const AdjointParams P, const De
     const float ln10 = 2.302585092994046f;
     for (long long i = gw; i < n_in; i += nw) {
         const PartRec pr = P.prec[i];
-        const int s = P.sorted_keys[i];
+        const int s = P.sorted_keys[i] / P.n_bands;
         const int p = P.perm[i];
         int ia, iz;
         float ta, tz, dta, dtz;
-        ssp_cell_d(log10f(pr.age), P.ssp.la_nodes, P.ssp.n_age, ia, ta, dta);
-        ssp_cell_d(log10f(pr.Z), P.ssp.lz_nodes, P.ssp.n_Z, iz, tz, dtz);
+        ssp_cell(log10f(pr.age), P.ssp.la_nodes, P.ssp.n_age, ia, ta, dta);
+        ssp_cell(log10f(pr.Z), P.ssp.lz_nodes, P.ssp.n_Z, iz, tz, dtz);
         const float w0 = (1.f - ta) * (1.f - tz), w1 = ta * (1.f - tz), w2 = (1.f - ta) * tz, w3 = ta * tz;
         const int c0 = ia * P.ssp.n_Z + iz;
         const int r0 = c0, r1 = c0 + da, r2 = c0 + dz, r3 = c0 + da + dz;

@@ -97,7 +97,9 @@ struct rubix_cube {
     size_t dep_smem = 0;
     int* d_tile_klo = nullptr;
     CUtensorMap tmap{};
-    int dep_ctas = 0, dep_threads = 512;
+    int dep_ctas = 0, dep_threads = RUBIX_DEP_THREADS;
+    int n_bands = 1, apb = 1;           // age bands of the template grid (sort key = spaxel * n_bands + band)
+    int band_row0[kMaxBands] = {};
     int chunk = 1024, cost_c0 = 2;
     // scratch
     long long cap = 0;
@@ -327,34 +329,60 @@ extern "C" rubix_status rubix_cube_create(const rubix_ssp_grid* ssp, const rubix
 
     // ---- deposit geometry: wavelength tiles and the SSP slab staged per tile ----
     {
+        // The slab holds one age band of templates x (tile nodes + Doppler halo).
+        // A tile is R rounds of 31 bins; choose the fewest bands that give R >= 5
+        // (the per-particle setup is shared by R rounds).
         const int align = 16 / h->elem;  // TMA: 16-byte aligned innermost coordinate and extent
-        h->n_boxes = (S.n_t + 255) / 256;
-        h->box_rows = ((S.n_t + h->n_boxes - 1) / h->n_boxes + 7) / 8 * 8;
-        h->n_rows_alloc = h->n_boxes * h->box_rows;
-        long long wcap = ((long long)smem_optin - 128) / ((long long)h->n_rows_alloc * h->elem);
-        wcap = std::min<long long>(wcap, 256);
-        wcap -= wcap % align;
         const double v_halo = 800.0;
         const double lam_max = (tel->lambda0 + (tel->n_lambda - 1) * tel->dlambda) / (1.0 + tel->z_cosmo);
         const double shift = lam_max / S.dls * (v_halo / kC_kms) / (1.0 - v_halo / kC_kms);
-        int R = 0;
-        for (int r = 8; r >= 1; --r) {
-            const double need = (32.0 * r - 1.0) * A0 * (1.0 + v_halo / kC_kms) + 2.0 * shift + 2.0 + (align - 1);
-            if (need <= (double)wcap) { R = r; break; }
+        const int cells = std::max(S.n_age - 1, 1);
+        struct Geo { int bands, apb, box_rows, n_boxes, rows_alloc, R; long long wcap; };
+        Geo best{0, 0, 0, 0, 0, 0, 0}, widest{0, 0, 0, 0, 0, 0, -1};
+        for (int nb = 1; nb <= kMaxBands; ++nb) {
+            if (nb > 1 && S.n_age < 3) break;
+            const int apb = (cells + nb - 1) / nb;
+            if (nb > 1 && (nb - 1) * apb >= cells) continue;  // a band would be empty
+            const int cols = (S.n_age >= 2) ? std::min(apb + 1, S.n_age) : 1;
+            const int rows = cols * S.n_Z;
+            const int n_boxes = (rows + 255) / 256;
+            const int box_rows = ((rows + n_boxes - 1) / n_boxes + 7) / 8 * 8;
+            const int rows_alloc = n_boxes * box_rows;
+            long long wcap = ((long long)smem_optin - 128) / ((long long)rows_alloc * h->elem);
+            wcap = std::min<long long>(wcap, 256);
+            wcap -= wcap % align;
+            int R = 0;
+            for (int r = 6; r >= 1; --r) {
+                const double span = std::max(31.0 * r + 1.0, (31.0 * r - 1.0) * A0 * (1.0 + v_halo / kC_kms) + 2.0);
+                const double need = span + 2.0 * shift + (align - 1);
+                if (need <= (double)wcap) { R = r; break; }
+            }
+            if (R > best.R) best = Geo{nb, apb, box_rows, n_boxes, rows_alloc, R, wcap};
+            if (wcap > widest.wcap) widest = Geo{nb, apb, box_rows, n_boxes, rows_alloc, 1, wcap};
+            if (best.R >= 5) break;
         }
-        if (R == 0) {
-            const double need1 = 31.0 * A0 + 2.0 + (align - 1) + 2.0;
-            R = 1;
-            if (need1 > (double)wcap) wcap = 0;  // slab cannot hold a tile: global-memory path only
+        if (best.R == 0) {
+            // not even 31 bins fit with the full halo: widest slab, 31-bin tiles,
+            // smaller halo; if a tile does not fit at all, global-memory path only
+            best = widest;
+            if (std::max(32.0, 30.0 * A0 + 2.0) + (align - 1) > (double)best.wcap) best.wcap = 0;
         }
-        h->tile_w = 32 * R;
+        const long long wcap = best.wcap;
+        const int R = best.R;
+        h->n_bands = best.bands;
+        h->apb = best.apb;
+        h->n_boxes = best.n_boxes;
+        h->box_rows = best.box_rows;
+        h->n_rows_alloc = best.rows_alloc;
+        for (int b = 0; b < kMaxBands; ++b) h->band_row0[b] = std::min(b * best.apb, std::max(S.n_age - 1, 0)) * S.n_Z;
+        h->tile_w = 31 * R;
         h->n_tiles = (tel->n_lambda + h->tile_w - 1) / h->tile_w;
         h->slab_w = (int)wcap;
         std::vector<int> klo(h->n_tiles, 0);
         for (int t = 0; t < h->n_tiles; ++t) {
             const int j0 = t * h->tile_w;
             const double t00 = ((tel->lambda0 + j0 * tel->dlambda) / (1.0 + tel->z_cosmo) - S.ls0) / S.dls;
-            const double span0 = (h->tile_w - 1) * A0 + 2.0;
+            const double span0 = std::max(31.0 * R + 1.0, (h->tile_w - 1) * A0 + 2.0);
             long long k = (long long)std::floor(t00 + 0.5 * span0 - 0.5 * h->slab_w);
             long long ka = k >= 0 ? (k / align) * align : -(((-k) + align - 1) / align) * align;
             if (ka < -(1ll << 20)) ka = -(1ll << 20);
@@ -384,7 +412,7 @@ extern "C" rubix_status rubix_cube_create(const rubix_ssp_grid* ssp, const rubix
 
     // ---- fixed-size device buffers ----
     const size_t cube_n = (size_t)h->n_s * tel->n_lambda;
-    if (dalloc(&h->d_seg_off, h->n_s + 2) || dalloc(&h->d_n_items, h->n_s + 1) || dalloc(&h->d_n_parts, h->n_s + 1) ||
+    if (dalloc(&h->d_seg_off, (size_t)h->n_s * h->n_bands + 2) || dalloc(&h->d_n_items, h->n_s + 1) || dalloc(&h->d_n_parts, h->n_s + 1) ||
         dalloc(&h->d_item_off, h->n_s + 1) || dalloc(&h->d_part_off, h->n_s + 1) ||
         dalloc(&h->d_scan_scratch, scan_scratch_ints(h->n_s + 1) + 16) || dalloc(&h->d_cube0, cube_n) ||
         dalloc(&h->d_tmp, cube_n) || dalloc(&h->d_err, 4) || dalloc(&h->d_slow, 1) || dalloc(&h->d_red, 1024))
@@ -447,8 +475,13 @@ static rubix_status run_assign_sort(rubix_cube* h, const rubix_particles* p, con
     A.ny = h->tel.ny;
     A.key = h->d_key;
     A.v_out = h->d_v;
+    A.age = arrs[8];
+    A.la_nodes = h->d_la;
+    A.n_age = h->ssp.n_age;
+    A.apb = h->apb;
+    A.n_bands = h->n_bands;
     h->launches += launch_assign(A, st);
-    h->launches += launch_sort_by_key(h->d_key, p->n, h->n_s + 1, h->d_keys_tmp, h->d_vals_tmp, h->d_skeys,
+    h->launches += launch_sort_by_key(h->d_key, p->n, h->n_s * h->n_bands + 1, h->d_keys_tmp, h->d_vals_tmp, h->d_skeys,
                                       h->d_perm, h->d_seg_off, h->d_sort_scratch, st);
     return RUBIX_OK;
 }
@@ -508,7 +541,7 @@ extern "C" rubix_status rubix_cube_forward(rubix_cube_t* h, const rubix_particle
         s = run_assign_sort(h, p, arrs, st);
         if (s != RUBIX_OK) return s;
     } else {
-        CK(cudaMemsetAsync(h->d_seg_off, 0, (h->n_s + 2) * sizeof(int), st));
+        CK(cudaMemsetAsync(h->d_seg_off, 0, ((size_t)h->n_s * h->n_bands + 2) * sizeof(int), st));
     }
     rec_ev(h, 1, st);
     SetupParams SP{};
@@ -516,6 +549,7 @@ extern "C" rubix_status rubix_cube_forward(rubix_cube_t* h, const rubix_particle
     SP.perm = h->d_perm;
     SP.seg_off = h->d_seg_off;
     SP.n_s = h->n_s;
+    SP.n_bands = h->n_bands;
     SP.mass = arrs[7];
     SP.age = arrs[8];
     SP.Z = arrs[9];
@@ -532,6 +566,7 @@ extern "C" rubix_status rubix_cube_forward(rubix_cube_t* h, const rubix_particle
     ItemParams IP{};
     IP.seg_off = h->d_seg_off;
     IP.n_s = h->n_s;
+    IP.n_bands = h->n_bands;
     IP.chunk = h->chunk;
     IP.n_items = h->d_n_items;
     IP.n_parts = h->d_n_parts;
@@ -551,6 +586,8 @@ extern "C" rubix_status rubix_cube_forward(rubix_cube_t* h, const rubix_particle
     DP.item_off = h->d_item_off;
     DP.seg_off = h->d_seg_off;
     DP.n_s = h->n_s;
+    DP.n_bands = h->n_bands;
+    for (int b = 0; b < kMaxBands; ++b) DP.band_row0[b] = h->band_row0[b];
     DP.n_lambda = h->tel.n_lambda;
     DP.tile_w = h->tile_w;
     DP.n_tiles = h->n_tiles;
@@ -639,7 +676,13 @@ extern "C" rubix_status rubix_cube_sorted(rubix_cube_t* h, int32_t* perm_out, in
     CK(cudaSetDevice(h->device));
     if (perm_out && h->last_n > 0)
         CK(cudaMemcpyAsync(perm_out, h->d_perm, (size_t)h->last_n * 4, cudaMemcpyDeviceToDevice, st));
-    if (seg_off_out) CK(cudaMemcpyAsync(seg_off_out, h->d_seg_off, (size_t)(h->n_s + 2) * 4, cudaMemcpyDeviceToDevice, st));
+    if (seg_off_out) {
+        // spaxel boundaries are every n_bands-th entry of the (spaxel, band) offsets
+        CK(cudaMemcpy2DAsync(seg_off_out, 4, h->d_seg_off, 4 * (size_t)h->n_bands, 4, (size_t)h->n_s + 1,
+                             cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(seg_off_out + h->n_s + 1, h->d_seg_off + (size_t)h->n_s * h->n_bands + 1, 4,
+                           cudaMemcpyDeviceToDevice, st));
+    }
     return RUBIX_OK;
 }
 
@@ -702,12 +745,13 @@ extern "C" rubix_status rubix_cube_stats(rubix_cube_t* h, int64_t* stats, int32_
     int n_in = 0;
     unsigned long long slow = 0;
     unsigned err = 0;
-    if (h->have_forward) CK(cudaMemcpy(&n_in, h->d_seg_off + h->n_s, 4, cudaMemcpyDeviceToHost));
+    if (h->have_forward)
+        CK(cudaMemcpy(&n_in, h->d_seg_off + (size_t)h->n_s * h->n_bands, 4, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&slow, h->d_slow, 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
-    int64_t v[8] = {n_in, (int64_t)n_in * h->tel.n_lambda, (int64_t)slow, h->dep_launches, h->launches,
-                    (int64_t)err, h->tile_w, h->slab_w};
-    const int n = std::min<int>(*n_inout, 8);
+    int64_t v[9] = {n_in, (int64_t)n_in * h->tel.n_lambda, (int64_t)slow, h->dep_launches, h->launches,
+                    (int64_t)err, h->tile_w, h->slab_w, h->n_bands};
+    const int n = std::min<int>(*n_inout, 9);
     for (int i = 0; i < n; ++i) stats[i] = v[i];
     *n_inout = n;
     return RUBIX_OK;
@@ -738,6 +782,7 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     P.seg_off = h->d_seg_off;
     P.sorted_keys = h->d_skeys;
     P.n_s = h->n_s;
+    P.n_bands = h->n_bands;
     P.n_lambda = h->tel.n_lambda;
     P.l0 = h->tel.lambda0;
     P.dl = h->tel.dlambda;
@@ -751,7 +796,8 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     P.contrib = d_global ? h->d_contrib : nullptr;
     P.n_in = h->last_n;  // upper bound; the kernel reads the in-field count on the device
     launch_adjoint_rec(P, h->d_rec, st);
-    if (d_global) launch_reduce_global(h->d_contrib, h->d_seg_off + h->n_s, d_global, h->d_red, st);
+    if (d_global)
+        launch_reduce_global(h->d_contrib, h->d_seg_off + (size_t)h->n_s * h->n_bands, d_global, h->d_red, st);
     CK(cudaGetLastError());
     return RUBIX_OK;
 }

@@ -113,6 +113,34 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(U4 ctr, uint32_t k0, uint32
 }
 
 // ----------------------------------------------------------------------------
+// SSP cell search: half-open cell [node_i, node_i+1) holding q, clamped outside
+// the grid (t = 0 below the first node, t = 1 at or above the last); dt = dt/dq
+// inside the grid, 0 when clamped. Shared by the key, setup and adjoint kernels
+// so that they always agree on the cell of a particle.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void ssp_cell(float q, const float* __restrict__ nodes, int n, int& i, float& t,
+                                         float& dt) {
+    if (n < 2 || !(q > nodes[0])) { i = 0; t = 0.f; dt = 0.f; return; }
+    if (q >= nodes[n - 1]) { i = n - 2; t = 1.f; dt = 0.f; return; }
+    int lo = 0, hi = n - 1;  // nodes[lo] <= q < nodes[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (nodes[mid] <= q) lo = mid; else hi = mid;
+    }
+    i = lo;
+    const float h = nodes[lo + 1] - nodes[lo];
+    t = (q - nodes[lo]) / h;
+    dt = 1.f / h;
+}
+
+// Age band of an age cell: the template grid is split into n_bands groups of
+// `apb` age cells so that one band's templates fit a wide shared-memory slab.
+__device__ __forceinline__ int age_band(int ia, int apb, int n_bands) {
+    const int b = (apb > 0) ? ia / apb : 0;
+    return b < n_bands - 1 ? b : n_bands - 1;
+}
+
+// ----------------------------------------------------------------------------
 // Work descriptors
 // ----------------------------------------------------------------------------
 // Per in-field particle, in sorted order: everything the deposit needs (32 B).

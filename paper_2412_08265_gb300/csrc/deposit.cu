@@ -3,17 +3,35 @@
 // population (SSP) library ... Doppler shifted ... resampling ... the stellar
 // spectra in each spaxel are summed up").
 //
-// K3 (k_setup) turns each in-field particle, in spaxel-sorted order, into a
-// 32-byte record: its four mass-scaled bilinear corner weights, the template
-// row of the (ia, iz) corner and the affine map from output bin j to the
-// fractional SSP node position t(j). K4 (k_deposit) is persistent: each CTA
-// owns a contiguous, cost-balanced range of (wavelength tile, work item)
-// pairs; for each tile it stages the SSP slab (all templates x the tile's
-// node range plus a Doppler halo) in shared memory with TMA, and its warps
-// accumulate whole items (<= chunk particles of one spaxel) in registers in a
-// fixed particle order. Spaxels with more than `chunk` particles are split
-// into several items whose FP32 partial rows K5 adds in FP64 in item order, so
-// the cube is bitwise reproducible and no global atomics are used.
+// K3 (k_setup) turns each in-field particle, in sorted order, into a 32-byte
+// record: its four mass-scaled bilinear corner weights, the template row of
+// the (ia, iz) corner and the affine map t(j) = B + jA from output bin j to
+// the fractional SSP node position.
+//
+// K4 (k_deposit) is persistent: each CTA owns a contiguous, cost-balanced range
+// of (wavelength tile, work item) pairs, a work item being <= chunk particles
+// of one spaxel. For each tile the CTA stages SSP slabs in shared memory with
+// TMA -- all templates of one age band x the tile's node range plus a Doppler
+// halo (TMA's zero fill outside the SSP range is the template's zero
+// extension) -- and its warps accumulate whole items in registers in a fixed
+// particle order. Particles are sorted by (spaxel, age band), so for band b
+// each item's band-b particles are contiguous; band 0 writes the item's row
+// and later bands add to it, in band order.
+//
+// Inner loop (one warp per particle, R rounds of 31 consecutive bins; lane l
+// owns bin j0 + 31 r + l): with dt/dj = A in (1 - 1/31, 1] and the round's
+// first bin at node position K0 + phi0, bin l sits at K0 + l + g with
+// g = phi0 - l (1 - A) in (-1, 1). Lane l forms the mass-weighted
+// interpolated template M = sum_c W_c T_c[K0 + l] (4 shared-memory loads at
+// consecutive addresses across the warp: no bank conflicts) and takes the
+// neighbouring node's M from lane l - 1 or l + 1 with one shuffle; the bin
+// value is M + g (M_next - M) or M + g (M - M_prev). Lane 31 only supplies
+// node K0 + 31. Other dt/dj, or Doppler shifts beyond the slab's halo, take a
+// per-bin path.
+//
+// Spaxels with more than `chunk` particles are split into several items whose
+// FP32 partial rows K5 adds in FP64 in item order, so the cube is bitwise
+// reproducible and no global atomics are used.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -22,21 +40,8 @@ namespace rubix {
 // ----------------------------------------------------------------------------
 // K3: per-particle setup (sorted order).
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void ssp_cell(float q, const float* __restrict__ nodes, int n, int& i, float& t) {
-    // half-open cell [node_i, node_i+1) holding q; clamped outside the grid
-    if (n < 2 || !(q > nodes[0])) { i = 0; t = 0.f; return; }
-    if (q >= nodes[n - 1]) { i = n - 2; t = 1.f; return; }
-    int lo = 0, hi = n - 1;  // nodes[lo] <= q < nodes[hi]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (nodes[mid] <= q) lo = mid; else hi = mid;
-    }
-    i = lo;
-    t = (q - nodes[lo]) / (nodes[lo + 1] - nodes[lo]);
-}
-
 __global__ void k_setup(SetupParams P) {
-    const long long n_in = P.seg_off[P.n_s];
+    const long long n_in = P.seg_off[(long long)P.n_s * P.n_bands];
     if (n_in > P.n_cap) return;
     const int n_ls = P.ssp.n_ls;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_in;
@@ -45,9 +50,9 @@ __global__ void k_setup(SetupParams P) {
         const float m = P.mass[p], age = P.age[p], Z = P.Z[p];
         const double v = P.v[p];
         int ia, iz;
-        float ta, tz;
-        ssp_cell(log10f(age), P.ssp.la_nodes, P.ssp.n_age, ia, ta);
-        ssp_cell(log10f(Z), P.ssp.lz_nodes, P.ssp.n_Z, iz, tz);
+        float ta, tz, dta, dtz;
+        ssp_cell(log10f(age), P.ssp.la_nodes, P.ssp.n_age, ia, ta, dta);
+        ssp_cell(log10f(Z), P.ssp.lz_nodes, P.ssp.n_Z, iz, tz, dtz);
         const float ms = (float)P.flux_scale * m;
         DepRec r;
         r.w[0] = ms * ((1.f - ta) * (1.f - tz));
@@ -64,7 +69,8 @@ __global__ void k_setup(SetupParams P) {
         int bi = 0;
         float bf = 0.f, a_hi = 0.f, a_lo = 0.f;
         if (!(dop > 0.0) || !(B < (double)n_ls) || !(t_last >= -1.0) || !(B > -32768.0)) {
-            r.w[0] = r.w[1] = r.w[2] = r.w[3] = 0.f;  // contributes nothing to any bin
+            // the spectrum misses every output bin (a_hi = 0 marks the record)
+            r.w[0] = r.w[1] = r.w[2] = r.w[3] = 0.f;
         } else {
             const double fb = floor(B);
             bi = (int)fb;
@@ -93,24 +99,26 @@ int launch_setup(const SetupParams& P, long long n_total, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------------------------
-// Work items: one per <= chunk particles of a spaxel; empty spaxels get one
-// empty item (its row is written as zeros).
+// Work items: one per <= chunk particles of a spaxel (all age bands); empty
+// spaxels get one empty item (its row is written as zeros).
 // ----------------------------------------------------------------------------
 __global__ void k_item_counts(ItemParams P) {
+    const int nb = P.n_bands;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= P.n_s; s += gridDim.x * blockDim.x) {
         if (s == P.n_s) { P.n_items[s] = 0; P.n_parts[s] = 0; continue; }
-        int cnt = P.seg_off[s + 1] - P.seg_off[s];
-        int ni = cnt > 0 ? (cnt + P.chunk - 1) / P.chunk : 1;
+        const int cnt = P.seg_off[(long long)(s + 1) * nb] - P.seg_off[(long long)s * nb];
+        const int ni = cnt > 0 ? (cnt + P.chunk - 1) / P.chunk : 1;
         P.n_items[s] = ni;
         P.n_parts[s] = ni > 1 ? ni : 0;
     }
 }
 
 __global__ void k_item_fill(ItemParams P) {
+    const int nb = P.n_bands;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.n_s; s += gridDim.x * blockDim.x) {
         const int base = P.item_off[s], ni = P.item_off[s + 1] - base;
         const bool split = P.part_off[s + 1] > P.part_off[s];
-        const int b0 = P.seg_off[s], e0 = P.seg_off[s + 1];
+        const int b0 = P.seg_off[(long long)s * nb], e0 = P.seg_off[(long long)(s + 1) * nb];
         for (int i = 0; i < ni; ++i) {
             if ((long long)base + i >= P.item_cap) { atomicOr(P.err, kErrBadItem); return; }
             Item it;
@@ -143,17 +151,16 @@ size_t deposit_smem_bytes(int n_rows_alloc, int slab_w, int elem_bytes) {
     return kDepHeader + (size_t)n_rows_alloc * slab_w * elem_bytes;
 }
 
-// First item index i in [0, n] with items[i].begin + c0 * i >= x (items[n] is
-// the virtual end with begin = n_in).
-__device__ __forceinline__ long long item_lower_bound(const Item* __restrict__ items, long long n, long long n_in,
-                                                      long long c0, long long x) {
+// First item index i in [0, n] with items[i].begin + c0 * i >= x (item n is
+// the virtual end).
+__device__ __forceinline__ long long item_lower_bound(const Item* __restrict__ items, long long n, long long c0,
+                                                      long long x) {
     long long lo = 0, hi = n;
     while (lo < hi) {
-        long long mid = (lo + hi) >> 1;
-        long long pre = (long long)items[mid].begin + c0 * mid;
+        const long long mid = (lo + hi) >> 1;
+        const long long pre = (long long)items[mid].begin + c0 * mid;
         if (pre < x) lo = mid + 1; else hi = mid;
     }
-    (void)n_in;
     return lo;
 }
 
@@ -162,15 +169,155 @@ __device__ __forceinline__ float tpl_global(const T* __restrict__ tpl, int pitch
     return (k >= 0 && k < n_ls) ? TplTraits<T>::ld(tpl + (long long)row * pitch + k) : 0.f;
 }
 
+// Node position of output bin j: t(j) = K + phi, phi in [0, 1). j*a_hi is
+// exact in FP32; only the small j*a_lo term is rounded.
+__device__ __forceinline__ int node_pos(int j, int bi, float bf, float a_hi, float a_lo, float& phi) {
+    const float jf = (float)j;
+    const float pp = jf * a_hi;
+    const float pi = floorf(pp);
+    const float s = (pp - pi) + fmaf(jf, a_lo, bf);
+    const float fl = floorf(s);
+    phi = s - fl;
+    return bi + (int)pi + (int)fl;
+}
+
+struct TileCtx {
+    int j0, klo, slab_w, row0, da, dz, n_lambda, pitch, n_ls;
+};
+
+// Per-bin evaluation for the general path: does bin j's node pair lie in the slab?
+__device__ __noinline__ bool bin_in_slab(const float4 w4, const float4 g4, const TileCtx C, int j, int lane) {
+    if (lane == 31 || j >= C.n_lambda) return true;
+    const int c0_bi = __float_as_int(g4.x);
+    float f;
+    const int k = node_pos(j, rec_bi(c0_bi), g4.y, g4.z, g4.w, f) - C.klo;
+    return k >= 0 && k + 1 < C.slab_w;
+}
+
+// Spectrum value of one particle at bin j (0 for lane 31 and bins past the end),
+// templates from the slab or, with use_slab false, from global memory.
+template <typename T>
+__device__ __noinline__ float bin_value(const float4 w4, const float4 g4, const TileCtx C, int j, int lane,
+                                        bool use_slab, const T* __restrict__ slab, const T* __restrict__ tpl) {
+    if (lane == 31 || j >= C.n_lambda) return 0.f;
+    const int c0_bi = __float_as_int(g4.x);
+    const int c0 = rec_c0(c0_bi);
+    float f;
+    const int k = node_pos(j, rec_bi(c0_bi), g4.y, g4.z, g4.w, f);
+    const int rows[4] = {c0, c0 + C.da, c0 + C.dz, c0 + C.da + C.dz};
+    const float ws[4] = {w4.x, w4.y, w4.z, w4.w};
+    float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (use_slab) {
+            const T* p = slab + (rows[c] - C.row0) * C.slab_w + (k - C.klo);
+            m0 = fmaf(ws[c], TplTraits<T>::ld(p), m0);
+            m1 = fmaf(ws[c], TplTraits<T>::ld(p + 1), m1);
+        } else {
+            m0 = fmaf(ws[c], tpl_global(tpl, C.pitch, C.n_ls, rows[c], k), m0);
+            m1 = fmaf(ws[c], tpl_global(tpl, C.pitch, C.n_ls, rows[c], k + 1), m1);
+        }
+    }
+    return fmaf(f, m1 - m0, m0);
+}
+
+// Adds one particle's spectrum to acc: acc[r] of lane l (l < 31) is output bin
+// j0 + 31 r + l.
 template <typename T, int R>
-__global__ void __launch_bounds__(512, 1) k_deposit(const DepositParams P, const __grid_constant__ CUtensorMap tmap) {
+__device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g4, const TileCtx& C,
+                                                 const T* __restrict__ slab, const T* __restrict__ tpl, int lane,
+                                                 float (&acc)[R], unsigned long long* slow_count) {
+    const int c0_bi = __float_as_int(g4.x);
+    const int c0 = rec_c0(c0_bi), bi = rec_bi(c0_bi);
+    const float bf = g4.y, a_hi = g4.z, a_lo = g4.w;
+    float phi0;
+    int K0 = node_pos(C.j0, bi, bf, a_hi, a_lo, phi0);  // node position of the round's first bin
+    const float delta = (1.f - a_hi) - a_lo;            // 1 - dt/dj (exact up to one rounding)
+    const int kw = K0 - C.klo;
+    // fast path (warp-uniform test): dt/dj in (1 - 1/31, 1] and every node the
+    // rounds read, K0 .. K0 + 31 R, inside the slab
+    if (C.slab_w > 0 && delta >= 0.f && delta * 31.f < 1.f && kw >= 0 && kw + 31 * R < C.slab_w) {
+        const float ldel = (float)lane * delta;
+        const float d31 = 31.f * delta;
+        const T* p00 = slab + (c0 - C.row0) * C.slab_w + kw + lane;
+        const T* p10 = p00 + C.da * C.slab_w;
+        const int oz = C.dz * C.slab_w;
+        // round r starts at node K0 + off[r] with fraction ph[r] (t advances by
+        // 31 dt/dj = 31 - 31 delta per round); warp-uniform, computed up front
+        int off[R];
+        float ph[R];
+        {
+            float f = phi0;
+            int o = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                off[r] = o;
+                ph[r] = f;
+                f -= d31;
+                const bool carry = f < 0.f;
+                f = carry ? f + 1.f : f;
+                o += carry ? 30 : 31;
+            }
+        }
+        const float2 wx = make_float2(w4.x, w4.x), wy = make_float2(w4.y, w4.y);
+        const float2 wz = make_float2(w4.z, w4.z), ww = make_float2(w4.w, w4.w);
+        const float2 nl = make_float2(-ldel, -ldel);
+#pragma unroll
+        for (int r = 0; r < R; r += 2) {
+            if (r + 1 < R) {
+                // two rounds at once in packed FP32x2: M at node K0 + off + lane
+                const int o0 = off[r], o1 = off[r + 1];
+                float2 M = __fmul2_rn(wx, make_float2(TplTraits<T>::ld(p00 + o0), TplTraits<T>::ld(p00 + o1)));
+                M = __ffma2_rn(wy, make_float2(TplTraits<T>::ld(p10 + o0), TplTraits<T>::ld(p10 + o1)), M);
+                M = __ffma2_rn(wz, make_float2(TplTraits<T>::ld(p00 + oz + o0), TplTraits<T>::ld(p00 + oz + o1)), M);
+                M = __ffma2_rn(ww, make_float2(TplTraits<T>::ld(p10 + oz + o0), TplTraits<T>::ld(p10 + oz + o1)), M);
+                // bins j0 + 31 r + lane sit at node K0 + off + lane + g, g in (-1, 1);
+                // the neighbour node on g's side comes from lane -+ 1:
+                // value = M + |g| (M_neighbour - M)
+                const float2 g = __fadd2_rn(make_float2(ph[r], ph[r + 1]), nl);
+                float2 X;
+                X.x = __shfl_sync(0xffffffffu, M.x, g.x < 0.f ? lane - 1 : lane + 1);
+                X.y = __shfl_sync(0xffffffffu, M.y, g.y < 0.f ? lane - 1 : lane + 1);
+                const float2 D = __fadd2_rn(X, make_float2(-M.x, -M.y));
+                float2 a = __fadd2_rn(make_float2(acc[r], acc[r + 1]), M);
+                a = __ffma2_rn(make_float2(fabsf(g.x), fabsf(g.y)), D, a);
+                acc[r] = a.x;
+                acc[r + 1] = a.y;
+            } else {
+                const int o0 = off[r];
+                float M = w4.x * TplTraits<T>::ld(p00 + o0);
+                M = fmaf(w4.y, TplTraits<T>::ld(p10 + o0), M);
+                M = fmaf(w4.z, TplTraits<T>::ld(p00 + oz + o0), M);
+                M = fmaf(w4.w, TplTraits<T>::ld(p10 + oz + o0), M);
+                const float g = ph[r] - ldel;
+                const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
+                acc[r] += fmaf(fabsf(g), X - M, M);
+            }
+        }
+        return;
+    }
+    // general path (out of line, rare on the workloads here): each bin's node
+    // pair from the slab if every bin of the warp is inside it, else from global
+    bool ok = C.slab_w > 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) ok = ok && bin_in_slab(w4, g4, C, C.j0 + 31 * i + lane, lane);
+    const bool use_slab = __all_sync(0xffffffffu, ok);
+    if (!use_slab && lane == 0 && slow_count) atomicAdd(slow_count, 1ull);
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] += bin_value<T>(w4, g4, C, C.j0 + 31 * i + lane, lane, use_slab, slab, tpl);
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const DepositParams P,
+                                                                   const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int* s_next = reinterpret_cast<int*>(smem + 16);
     T* slab = reinterpret_cast<T*>(smem + kDepHeader);
 
     const int lane = threadIdx.x & 31;
-    const long long n_in = P.seg_off[P.n_s];
+    const int nb = P.n_bands;
+    const long long n_in = P.seg_off[(long long)P.n_s * nb];
     const long long n_items = P.item_off[P.n_s];
     const long long C0 = P.cost_c0;
     const long long Ct = n_in + C0 * n_items;
@@ -187,119 +334,100 @@ __global__ void __launch_bounds__(512, 1) k_deposit(const DepositParams P, const
     __syncthreads();
 
     const T* __restrict__ tpl = reinterpret_cast<const T*>(P.ssp.tpl);
-    const int pitch = P.ssp.pitch, n_ls = P.ssp.n_ls;
-    const int da = (P.ssp.n_age > 1) ? P.ssp.n_Z : 0;
-    const int dz = (P.ssp.n_Z > 1) ? 1 : 0;
-    const int slab_w = P.slab_w;
+    const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(P.rec);
+    TileCtx C;
+    C.slab_w = P.slab_w;
+    C.da = (P.ssp.n_age > 1) ? P.ssp.n_Z : 0;
+    C.dz = (P.ssp.n_Z > 1) ? 1 : 0;
+    C.n_lambda = P.n_lambda;
+    C.pitch = P.ssp.pitch;
+    C.n_ls = P.ssp.n_ls;
     uint32_t phase = 0;
 
     for (long long t = lo / Ct; t < P.n_tiles && t * Ct < hi; ++t) {
         const long long a = max(lo - t * Ct, 0ll), b = min(hi - t * Ct, Ct);
         if (a >= b) continue;
-        const int i_a = (int)item_lower_bound(P.items, n_items, n_in, C0, a);
-        const int i_b = (int)item_lower_bound(P.items, n_items, n_in, C0, b);
+        const int i_a = (int)item_lower_bound(P.items, n_items, C0, a);
+        const int i_b = (int)item_lower_bound(P.items, n_items, C0, b);
         if (i_a >= i_b) continue;
-        const int klo = P.tile_klo[t];
+        C.klo = P.tile_klo[t];
+        C.j0 = (int)t * P.tile_w;
 
-        __syncthreads();  // all warps are done with the previous slab
-        if (threadIdx.x == 0) {
-            *s_next = i_a;
-            if (slab_w > 0) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, (uint32_t)(P.n_boxes * P.box_rows * slab_w * (int)sizeof(T)));
-                for (int bx = 0; bx < P.n_boxes; ++bx)
-                    tma_load_2d(slab + (size_t)bx * P.box_rows * slab_w, &tmap, bar, klo, bx * P.box_rows);
+        for (int band = 0; band < nb; ++band) {
+            C.row0 = P.band_row0[band];
+            __syncthreads();  // all warps are done with the previous slab and rows
+            if (threadIdx.x == 0) {
+                *s_next = i_a;
+                if (C.slab_w > 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(bar, (uint32_t)(P.n_boxes * P.box_rows * C.slab_w * (int)sizeof(T)));
+                    for (int bx = 0; bx < P.n_boxes; ++bx)
+                        tma_load_2d(slab + (size_t)bx * P.box_rows * C.slab_w, &tmap, bar, C.klo,
+                                    C.row0 + bx * P.box_rows);
+                }
             }
-        }
-        bool ok = true;
-        if (slab_w > 0) {
-            ok = mbar_wait_bounded(bar, phase, 4000000000ll);
-            phase ^= 1u;
-        }
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) atomicOr(P.err, kErrTmaTimeout);
-            return;
-        }
+            bool ok = true;
+            if (C.slab_w > 0) {
+                ok = mbar_wait_bounded(bar, phase, 4000000000ll);
+                phase ^= 1u;
+            }
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(P.err, kErrTmaTimeout);
+                return;
+            }
 
-        const int j0 = (int)t * P.tile_w;
-        while (true) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(s_next, 1);
-            it = __shfl_sync(0xffffffffu, it, 0);
-            if (it >= i_b) break;
-            const Item I = P.items[it];
-            float acc[R];
+            while (true) {
+                int it = 0;
+                if (lane == 0) it = atomicAdd(s_next, 1);
+                it = __shfl_sync(0xffffffffu, it, 0);
+                if (it >= i_b) break;
+                const Item I = P.items[it];
+                int qb = I.begin, qe = I.end;
+                if (nb > 1) {
+                    qb = max(qb, P.seg_off[(long long)I.spaxel * nb + band]);
+                    qe = min(qe, P.seg_off[(long long)I.spaxel * nb + band + 1]);
+                }
+                if (band > 0 && qb >= qe) continue;
+                if (I.part_row >= P.part_cap || I.spaxel < 0 || I.spaxel >= P.n_s) {
+                    if (lane == 0) atomicOr(P.err, kErrBadItem);
+                    continue;
+                }
+                float acc[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = 0.f;
-
-            for (int q = I.begin; q < I.end; ++q) {
-                const float4 w4 = reinterpret_cast<const float4*>(P.rec)[2 * q];
-                const float4 g4 = reinterpret_cast<const float4*>(P.rec)[2 * q + 1];
-                const int c0_bi = __float_as_int(g4.x);
-                const int c0 = rec_c0(c0_bi), bi = rec_bi(c0_bi);
-                const float bf = g4.y, a_hi = g4.z, a_lo = g4.w;
-                int kk[R];
-                float ff[R];
-                bool inr = true;
+                for (int r = 0; r < R; ++r) acc[r] = 0.f;
+                // records of the next RUBIX_DEP_PREFETCH particles are in flight
+                // while the current one is deposited
+                constexpr int PF = RUBIX_DEP_PREFETCH;
+                float4 wq[PF], gq[PF];
+#pragma unroll
+                for (int k = 0; k < PF; ++k)
+                    if (qb + k < qe) {
+                        wq[k] = rec4[2 * (qb + k)];
+                        gq[k] = rec4[2 * (qb + k) + 1];
+                    }
+                for (int q = qb; q < qe; ++q) {
+                    const float4 w4 = wq[0], g4 = gq[0];
+#pragma unroll
+                    for (int k = 0; k + 1 < PF; ++k) {
+                        wq[k] = wq[k + 1];
+                        gq[k] = gq[k + 1];
+                    }
+                    if (q + PF < qe) {
+                        wq[PF - 1] = rec4[2 * (q + PF)];
+                        gq[PF - 1] = rec4[2 * (q + PF) + 1];
+                    }
+                    deposit_particle<T, R>(w4, g4, C, slab, tpl, lane, acc, P.slow_count);
+                }
+                float* dst = (I.part_row < 0) ? P.cube + (long long)I.spaxel * P.n_lambda
+                                              : P.partials + (long long)I.part_row * P.n_lambda;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const int j = j0 + lane + 32 * r;
-                    const float jf = (float)j;
-                    const float pp = jf * a_hi;           // exact
-                    const float pi = floorf(pp);
-                    const float s = (pp - pi) + fmaf(jf, a_lo, bf);
-                    const float fl = floorf(s);
-                    ff[r] = s - fl;
-                    kk[r] = bi + (int)pi + (int)fl - klo;
-                    if (j < P.n_lambda) inr = inr && (kk[r] >= 0) && (kk[r] + 1 < slab_w);
-                }
-                if (__all_sync(0xffffffffu, inr)) {
-                    const T* s00 = slab + c0 * slab_w;
-                    const T* s10 = s00 + da * slab_w;
-                    const T* s01 = s00 + dz * slab_w;
-                    const T* s11 = s10 + dz * slab_w;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const int k = kk[r];
-                        if (j0 + lane + 32 * r < P.n_lambda) {
-                            const float m0 = w4.x * TplTraits<T>::ld(s00 + k) + w4.y * TplTraits<T>::ld(s10 + k) +
-                                             w4.z * TplTraits<T>::ld(s01 + k) + w4.w * TplTraits<T>::ld(s11 + k);
-                            const float m1 = w4.x * TplTraits<T>::ld(s00 + k + 1) +
-                                             w4.y * TplTraits<T>::ld(s10 + k + 1) +
-                                             w4.z * TplTraits<T>::ld(s01 + k + 1) +
-                                             w4.w * TplTraits<T>::ld(s11 + k + 1);
-                            acc[r] += fmaf(ff[r], m1 - m0, m0);
-                        }
-                    }
-                } else {
-                    if (lane == 0 && P.slow_count) atomicAdd(P.slow_count, 1ull);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const int k = kk[r] + klo;
-                        if (j0 + lane + 32 * r < P.n_lambda) {
-                            float m0 = 0.f, m1 = 0.f;
-                            const int rows[4] = {c0, c0 + da, c0 + dz, c0 + da + dz};
-                            const float ws[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                m0 += ws[c] * tpl_global(tpl, pitch, n_ls, rows[c], k);
-                                m1 += ws[c] * tpl_global(tpl, pitch, n_ls, rows[c], k + 1);
-                            }
-                            acc[r] += fmaf(ff[r], m1 - m0, m0);
-                        }
+                    const int j = C.j0 + 31 * r + lane;
+                    if (lane < 31 && j < P.n_lambda) {
+                        if (band == 0) dst[j] = acc[r];
+                        else dst[j] += acc[r];
                     }
                 }
-            }
-            if (I.part_row >= P.part_cap || I.spaxel < 0 || I.spaxel >= P.n_s) {
-                if (lane == 0) atomicOr(P.err, kErrBadItem);
-                continue;
-            }
-            float* dst = (I.part_row < 0) ? P.cube + (long long)I.spaxel * P.n_lambda
-                                          : P.partials + (long long)I.part_row * P.n_lambda;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int j = j0 + lane + 32 * r;
-                if (j < P.n_lambda) dst[j] = acc[r];
             }
         }
     }
@@ -308,17 +436,15 @@ __global__ void __launch_bounds__(512, 1) k_deposit(const DepositParams P, const
 template <typename T>
 static int launch_deposit_t(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,
                             cudaStream_t st) {
-    const int R = P.tile_w / 32;
+    if (P.tile_w % 31 != 0) return -1;
     void (*fn)(const DepositParams, const CUtensorMap) = nullptr;
-    switch (R) {
+    switch (P.tile_w / 31) {
         case 1: fn = k_deposit<T, 1>; break;
         case 2: fn = k_deposit<T, 2>; break;
         case 3: fn = k_deposit<T, 3>; break;
         case 4: fn = k_deposit<T, 4>; break;
         case 5: fn = k_deposit<T, 5>; break;
         case 6: fn = k_deposit<T, 6>; break;
-        case 7: fn = k_deposit<T, 7>; break;
-        case 8: fn = k_deposit<T, 8>; break;
         default: return -1;
     }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;

@@ -12,7 +12,19 @@ struct DepRec;
 struct PartRec;
 struct Item;
 
-// K1 parameters.
+constexpr int kMaxBands = 8;
+
+// Deposit launch shape: threads per CTA (one CTA per SM: the SSP slab fills
+// shared memory) and how many particle records a warp loads ahead.
+#ifndef RUBIX_DEP_THREADS
+#define RUBIX_DEP_THREADS 1024
+#endif
+#ifndef RUBIX_DEP_PREFETCH
+#define RUBIX_DEP_PREFETCH 1
+#endif
+
+// K1 parameters. The sort key is spaxel * n_bands + age band (n_bands <= 1:
+// the plain spaxel key); particles outside the field get nx*ny*n_bands.
 struct AssignParams {
     long long n;
     const float *x, *y, *z, *vy, *vz, *v_los;
@@ -22,6 +34,10 @@ struct AssignParams {
     int nx, ny;
     int* key;         // [n]
     double* v_out;    // [n] line-of-sight velocity (nullable)
+    // age bands (optional)
+    const float* age;
+    const float* la_nodes;
+    int n_age, apb, n_bands;
 };
 
 int launch_assign(const AssignParams& P, cudaStream_t st);
@@ -46,8 +62,8 @@ struct SspDev {
 struct SetupParams {
     SspDev ssp;
     const int* perm;         // sorted position -> particle index
-    const int* seg_off;      // [n_s + 2]
-    int n_s;
+    const int* seg_off;      // [n_s * n_bands + 2]
+    int n_s, n_bands;
     const float *mass, *age, *Z;
     const double* v;         // line-of-sight velocity per particle
     double l0, dl, z_cosmo, flux_scale;
@@ -59,8 +75,8 @@ struct SetupParams {
 int launch_setup(const SetupParams& P, long long n_total, cudaStream_t st);
 
 struct ItemParams {
-    const int* seg_off;      // [n_s + 2]
-    int n_s;
+    const int* seg_off;      // [n_s * n_bands + 2]
+    int n_s, n_bands;
     int chunk;               // max particles per item
     int* n_items;            // [n_s + 1] scratch
     int* n_parts;            // [n_s + 1] scratch
@@ -79,14 +95,16 @@ struct DepositParams {
     const DepRec* rec;
     const Item* items;
     const int* item_off;     // [n_s + 1]: total items at [n_s]
-    const int* seg_off;      // [n_s + 2]: in-field particles at [n_s]
+    const int* seg_off;      // [n_s * n_bands + 2]: in-field particles at [n_s * n_bands]
     int n_s;
+    int n_bands;
+    int band_row0[kMaxBands];  // first template row of each band's slab
     int n_lambda;
-    int tile_w;              // output bins per tile, multiple of 32
+    int tile_w;              // output bins per tile = 31 * rounds (1..6)
     int n_tiles;
     const int* tile_klo;     // [n_tiles] first SSP node of each tile's slab
     int slab_w;              // nodes per slab row (0 = no slab: global path only)
-    int box_rows, n_boxes;   // TMA boxes covering the template rows
+    int box_rows, n_boxes;   // TMA boxes covering one band's template rows
     int cost_c0;             // per-item cost in particle units
     float* cube;             // [n_s][n_lambda]
     float* partials;         // [n_parts][n_lambda]
@@ -119,14 +137,14 @@ struct AdjointParams {
     SspDev ssp;
     const PartRec* prec;       // [n_in] sorted order
     const int* perm;           // sorted position -> particle index
-    const int* seg_off;        // [n_s + 2]
-    const int* sorted_keys;    // [n] key per sorted position
-    int n_s, n_lambda;
+    const int* seg_off;        // [n_s * n_bands + 2]
+    const int* sorted_keys;    // [n] key per sorted position (spaxel * n_bands + band)
+    int n_s, n_bands, n_lambda;
     double l0, dl, z_cosmo, flux_scale;
     const float* G0;           // [n_s][n_lambda] dL/dcube0
     float *d_mass, *d_age, *d_Z, *d_v;   // original order, nullable
     double* contrib;           // [n_in][2] per sorted particle: dL/dv, m*dL/dm (FP64)
-    long long n_in;
+    long long n_in;            // upper bound (grid sizing)
 };
 int launch_adjoint_rec(const AdjointParams& P, const DepRec* rec, cudaStream_t st);
 int launch_zero_grads(float* a, float* b, float* c, float* d, long long n, cudaStream_t st);

@@ -12,6 +12,8 @@ namespace rubix {
 // v = vy sin i + vz cos i; x_lo = (-0.5 nx) size; u = (x' - x_lo) * (1/size);
 // every FP64 op rounded once (explicit _rn intrinsics, no contraction), so the
 // integer key is bit-identical to a host evaluation of the same expression.
+// With age bands the sort key appends the particle's band (an internal
+// partition of the SSP grid used by the deposit) below the spaxel index.
 // ----------------------------------------------------------------------------
 __global__ void k_assign(AssignParams P) {
     const long long n = P.n;
@@ -37,11 +39,19 @@ __global__ void k_assign(AssignParams P) {
         }
         double u = __dmul_rn(__dsub_rn(xp, P.x_lo), P.inv_size);
         double w = __dmul_rn(__dsub_rn(yp, P.y_lo), P.inv_size);
+        const int nb = P.n_bands > 1 ? P.n_bands : 1;
         int key;
-        if (u >= 0.0 && u < (double)P.nx && w >= 0.0 && w < (double)P.ny)
-            key = (int)w * P.nx + (int)u;
-        else
-            key = P.nx * P.ny;
+        if (u >= 0.0 && u < (double)P.nx && w >= 0.0 && w < (double)P.ny) {
+            key = ((int)w * P.nx + (int)u) * nb;
+            if (nb > 1) {
+                int ia;
+                float ta, dta;
+                ssp_cell(log10f(P.age[p]), P.la_nodes, P.n_age, ia, ta, dta);
+                key += age_band(ia, P.apb, nb);
+            }
+        } else {
+            key = P.nx * P.ny * nb;
+        }
         P.key[p] = key;
         if (P.v_out) P.v_out[p] = v;
     }

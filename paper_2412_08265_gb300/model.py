@@ -135,7 +135,7 @@ class CubeModel:
     def stats(self) -> dict:
         s = capi.rubix_cube_stats(self.handle)
         keys = ["n_in_fov", "deposits", "slow_particle_tiles", "deposit_launches", "kernel_launches",
-                "device_error", "tile_w", "slab_w"]
+                "device_error", "tile_w", "slab_w", "n_bands"]
         return dict(zip(keys, s))
 
     def set_profiling(self, on: bool = True):

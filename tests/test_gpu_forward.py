@@ -105,9 +105,31 @@ def test_sort_and_segments_bit_exact(torch_cuda):
     key = oracle.spaxel_keys(xp, yp, wl.telescope)
     n_s = wl.telescope.nx * wl.telescope.ny
     operm, oseg = oracle.stable_sort(key, n_s + 1)
-    assert np.array_equal(perm.cpu().numpy(), operm)
-    assert np.array_equal(seg.cpu().numpy().astype(np.int64), oseg)
+    seg = seg.cpu().numpy().astype(np.int64)
+    perm = perm.cpu().numpy()
+    assert np.array_equal(seg, oseg)
+    assert_same_segments_banded(perm, operm, seg, wl.particles.age, model.stats()["n_bands"])
     model.close()
+
+
+def assert_same_segments_banded(perm, operm, seg, age, n_bands):
+    """Unique part of the sort: each spaxel's set of particles. Within a spaxel
+    the deposit orders particles by SSP age band then index: at most n_bands
+    increasing runs, each run no older than the next."""
+    for s in range(len(seg) - 1):
+        a, b = int(seg[s]), int(seg[s + 1])
+        if b - a == 0:
+            continue
+        g, o = perm[a:b], operm[a:b]
+        assert np.array_equal(np.sort(g), o), s
+        if n_bands == 1 or s == len(seg) - 2:
+            assert np.array_equal(g, o), s
+            continue
+        breaks = np.flatnonzero(np.diff(g) < 0) + 1
+        runs = np.split(g, breaks)
+        assert len(runs) <= n_bands, s
+        for r0, r1 in zip(runs[:-1], runs[1:]):
+            assert age[r0].max() <= age[r1].min(), s
 
 
 # ---------------------------------------------------------------------------
