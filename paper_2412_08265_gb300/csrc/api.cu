@@ -100,7 +100,7 @@ struct rubix_cube {
     int dep_ctas = 0, dep_threads = RUBIX_DEP_THREADS;
     int n_bands = 1, apb = 1;           // age bands of the template grid (sort key = spaxel * n_bands + band)
     int band_row0[kMaxBands] = {};
-    int chunk = 1024, cost_c0 = 2;
+    int chunk = RUBIX_DEP_CHUNK, cost_c0 = 2;
     // scratch
     long long cap = 0;
     long long item_cap = 0, part_cap = 0;
@@ -333,7 +333,7 @@ extern "C" rubix_status rubix_cube_create(const rubix_ssp_grid* ssp, const rubix
         // A tile is R rounds of 31 bins; choose the fewest bands that give R >= 5
         // (the per-particle setup is shared by R rounds).
         const int align = 16 / h->elem;  // TMA: 16-byte aligned innermost coordinate and extent
-        const double v_halo = 800.0;
+        const double v_halo = RUBIX_DEP_VHALO;
         const double lam_max = (tel->lambda0 + (tel->n_lambda - 1) * tel->dlambda) / (1.0 + tel->z_cosmo);
         const double shift = lam_max / S.dls * (v_halo / kC_kms) / (1.0 - v_halo / kC_kms);
         const int cells = std::max(S.n_age - 1, 1);
@@ -359,7 +359,7 @@ extern "C" rubix_status rubix_cube_create(const rubix_ssp_grid* ssp, const rubix
             }
             if (R > best.R) best = Geo{nb, apb, box_rows, n_boxes, rows_alloc, R, wcap};
             if (wcap > widest.wcap) widest = Geo{nb, apb, box_rows, n_boxes, rows_alloc, 1, wcap};
-            if (best.R >= 5) break;
+            if (best.R >= RUBIX_DEP_MIN_R) break;
         }
         if (best.R == 0) {
             // not even 31 bins fit with the full halo: widest slab, 31-bin tiles,

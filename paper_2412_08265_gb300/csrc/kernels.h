@@ -22,6 +22,18 @@ constexpr int kMaxBands = 8;
 #ifndef RUBIX_DEP_PREFETCH
 #define RUBIX_DEP_PREFETCH 1
 #endif
+// Deposit geometry: particles per work item, the line-of-sight speed (km/s)
+// the shared-memory slab's Doppler halo covers, and the fewest 31-bin rounds
+// per wavelength tile worth adding age bands for.
+#ifndef RUBIX_DEP_CHUNK
+#define RUBIX_DEP_CHUNK 1024
+#endif
+#ifndef RUBIX_DEP_VHALO
+#define RUBIX_DEP_VHALO 800.0
+#endif
+#ifndef RUBIX_DEP_MIN_R
+#define RUBIX_DEP_MIN_R 5
+#endif
 
 // K1 parameters. The sort key is spaxel * n_bands + age band (n_bands <= 1:
 // the plain spaxel key); particles outside the field get nx*ny*n_bands.

@@ -3,14 +3,15 @@
 // noise"; Sec. 4: both Gaussian).
 //
 // The 3-D kernel is separable, g(dy) g(dx) h(dj), with zero padding on every
-// axis, so the PSF and LSF are applied as three 1-D stencils:
+// axis. For the radii of the instruments used here a single fused pass
+// (k_psf_lsf_fused, below) reads the cube once and writes it once. Other radii
+// take two passes through an intermediate cube:
 //   pass 1 (k_lsf_psfx): one CTA per (wavelength chunk, x chunk, row y) loads
 //     the row segment with its halos into shared memory, applies the LSF along
 //     wavelength and then the PSF along x, and writes an intermediate cube;
 //   pass 2 (k_psfy_noise): each thread owns one (x, wavelength) column of a
 //     y-chunk and applies the PSF along y, then optional Philox noise.
-// Both passes read and write along wavelength (the fastest axis), so every
-// global access is coalesced.
+// All global accesses run along wavelength (the fastest axis): coalesced.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -91,7 +92,183 @@ __global__ void __launch_bounds__(256) k_psfy_noise(const ConvParams P, const fl
     }
 }
 
+
+// ----------------------------------------------------------------------------
+// Fused single pass for the common radii (compile-time rp, rl): one CTA owns an
+// (x block of kFX spaxels, wavelength chunk of kFL = 32 bins, y band of kFY
+// rows) and streams the input rows of its band, plus rp halo rows, through a
+// cp.async pipeline (zero fill outside the cube). For each input row: LSF along
+// wavelength into shared memory (lanes run along wavelength, warps over x),
+// then PSF along x; the PSF-x value of input row y_in is added, with weight
+// gp[m], to the register accumulator of output row y_in - rp + m (the 2 rp + 1
+// accumulators of each owned (x, wavelength) rotate with the row, the loop
+// being unrolled by 2 rp + 1 so their indices are static). After row y_in the
+// accumulator of output row y_in - rp is complete: noise is added and it is
+// written once. The cube is read once (plus halos) and written once.
+// ----------------------------------------------------------------------------
+#ifndef RUBIX_PSF_STAGES
+#define RUBIX_PSF_STAGES 3      // input rows in flight (cp.async pipeline depth)
+#endif
+constexpr int kFX = 48, kFL = 32, kFY = 50;  // kFL must equal the warp width
+constexpr int kFThreads = 256;
+constexpr int kFWarps = kFThreads / 32;
+constexpr int kFXW = kFX / kFWarps;          // output x rows owned by each warp
+constexpr int kFStages = RUBIX_PSF_STAGES;
+
+template <int RP, int RL>
+constexpr size_t fused_smem_bytes() {
+    return sizeof(float) * ((size_t)kFStages * (kFX + 2 * RP) * (kFL + 2 * RL) + (size_t)(kFX + 2 * RP) * kFL);
+}
+
+__device__ __forceinline__ float add_noise(float v, long long idx, const ConvParams& P) {
+    U4 c;
+    c.x = (uint32_t)idx;
+    c.y = (uint32_t)((unsigned long long)idx >> 32);
+    c.z = 0u;
+    c.w = 0u;
+    const U4 r = philox4x32_10(c, P.seed_lo, P.seed_hi);
+    const float u1 = (float)((r.x >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
+    const float u2 = (float)(r.y >> 8) * (1.0f / 16777216.0f);         // [0, 1)
+    const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    return fmaf(fabsf(v) * P.noise_inv_s2n, z, v);
+}
+
+template <int RP, int RL>
+__global__ void __launch_bounds__(kFThreads) k_psf_lsf_fused(const ConvParams P, const float* __restrict__ in,
+                                                             float* __restrict__ out) {
+    constexpr int XW = kFX + 2 * RP, LW = kFL + 2 * RL, NR = 2 * RP + 1;
+    extern __shared__ float sm[];
+    float* s_in = sm;                        // [kFStages][XW][LW]
+    float* s_l = s_in + kFStages * XW * LW;  // [XW][kFL]   LSF output
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j0 = blockIdx.x * kFL;
+    const int x0 = blockIdx.y * kFX;
+    const int y0 = blockIdx.z * kFY;
+    const int y1 = min(y0 + kFY, P.ny);
+    const int nx = P.nx, ny = P.ny, nl = P.n_lambda;
+    const int n_rows = (y1 - y0) + 2 * RP;   // input rows y0 - RP .. y1 + RP - 1
+    float gl[2 * RL + 1], gp[NR];
+#pragma unroll
+    for (int d = 0; d <= 2 * RL; ++d) gl[d] = P.gl[d];
+#pragma unroll
+    for (int d = 0; d < NR; ++d) gp[d] = P.gp[d];
+
+    auto load_row = [&](int i, int buf) {
+        const int y = y0 - RP + i;
+        float* dst = s_in + buf * XW * LW;
+        const bool yok = (y >= 0 && y < ny);
+        for (int xi = warp; xi < XW; xi += kFWarps) {
+            const int x = x0 - RP + xi;
+            const bool xok = yok && x >= 0 && x < nx;
+            const float* row = in + ((long long)(xok ? y : 0) * nx + (xok ? x : 0)) * nl;
+#pragma unroll
+            for (int l = lane; l < LW; l += 32) {
+                const int j = j0 - RL + l;
+                const bool ok = xok && j >= 0 && j < nl;
+                cp_async4(dst + xi * LW + l, ok ? row + j : in, ok);
+            }
+        }
+        cp_async_commit();
+    };
+
+    float acc[kFXW][NR];
+#pragma unroll
+    for (int k = 0; k < kFXW; ++k)
+#pragma unroll
+        for (int m = 0; m < NR; ++m) acc[k][m] = 0.f;
+
+    for (int k = 0; k < kFStages - 1; ++k) {
+        if (k < n_rows) load_row(k, k);
+        else cp_async_commit();
+    }
+    int buf = 0;
+    const int j = j0 + lane;
+    for (int ib = 0; ib < n_rows; ib += NR) {
+#pragma unroll
+        for (int ph = 0; ph < NR; ++ph) {   // input row i = ib + ph; accumulator of row y_in - RP + m is (ph + m) % NR
+            const int i = ib + ph;
+            if (i < n_rows) {
+                const int ahead = i + kFStages - 1;
+                int abuf = buf + kFStages - 1;
+                if (abuf >= kFStages) abuf -= kFStages;
+                if (ahead < n_rows) load_row(ahead, abuf);  // that buffer was read in iteration i - 1
+                else cp_async_commit();
+                cp_async_wait<kFStages - 1>();
+                __syncthreads();  // row i landed; every warp is done with s_l of row i - 1
+                const float* src = s_in + buf * XW * LW;
+                if (++buf == kFStages) buf = 0;
+                for (int xi = warp; xi < XW; xi += kFWarps) {
+                    const float* r = src + xi * LW + lane;
+                    float a = 0.f;
+#pragma unroll
+                    for (int d = 0; d <= 2 * RL; ++d) a = fmaf(gl[d], r[d], a);
+                    s_l[xi * kFL + lane] = a;
+                }
+                __syncthreads();
+                const int y_done = y0 + i - 2 * RP;  // output row completed by this input row
+#pragma unroll
+                for (int k = 0; k < kFXW; ++k) {
+                    const int xi = warp + k * kFWarps;
+                    const float* c = s_l + xi * kFL + lane;
+                    float v = 0.f;
+#pragma unroll
+                    for (int d = 0; d < NR; ++d) v = fmaf(gp[d], c[d * kFL], v);
+#pragma unroll
+                    for (int m = 0; m < NR; ++m) acc[k][(ph + m) % NR] = fmaf(gp[m], v, acc[k][(ph + m) % NR]);
+                    // accumulator (ph + 0) % NR holds output row y_in - RP = y_done: complete
+                    float& done = acc[k][ph % NR];
+                    const int x = x0 + xi;
+                    if (y_done >= y0 && x < nx && j < nl) {
+                        const long long idx = ((long long)y_done * nx + x) * nl + j;
+                        out[idx] = (P.noise_inv_s2n > 0.f) ? add_noise(done, idx, P) : done;
+                    }
+                    done = 0.f;
+                }
+            }
+        }
+    }
+}
+
+template <int RP, int RL>
+static bool launch_fused(const ConvParams& P, const float* in, float* out, cudaStream_t st) {
+    constexpr size_t smem = fused_smem_bytes<RP, RL>();
+    static_assert(smem <= 200 * 1024, "fused PSF/LSF tile does not fit shared memory");
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_psf_lsf_fused<RP, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return false;
+        attr = true;
+    }
+    dim3 g((P.n_lambda + kFL - 1) / kFL, (P.nx + kFX - 1) / kFX, (P.ny + kFY - 1) / kFY);
+    k_psf_lsf_fused<RP, RL><<<g, kFThreads, smem, st>>>(P, in, out);
+    return true;
+}
+
+// Radii with a fused instantiation: the PSF of FWHM 1.5 spaxels (rp = 3) and
+// LSFs of sigma 1.2 A on 1.25 A or 3 A bins (rl = 4, 2), plus neighbours.
+static bool try_fused(const ConvParams& P, const float* in, float* out, cudaStream_t st) {
+#ifdef RUBIX_PSF_TWO_PASS
+    return false;
+#endif
+#define RUBIX_FUSED_CASE(RP_, RL_) \
+    if (P.rp == RP_ && P.rl == RL_) return launch_fused<RP_, RL_>(P, in, out, st);
+    RUBIX_FUSED_CASE(3, 4)
+    RUBIX_FUSED_CASE(3, 2)
+    RUBIX_FUSED_CASE(3, 0)
+    RUBIX_FUSED_CASE(0, 4)
+    RUBIX_FUSED_CASE(0, 2)
+    RUBIX_FUSED_CASE(2, 4)
+    RUBIX_FUSED_CASE(4, 4)
+    RUBIX_FUSED_CASE(3, 3)
+    RUBIX_FUSED_CASE(3, 5)
+#undef RUBIX_FUSED_CASE
+    return false;
+}
+
 int launch_psf_lsf(const ConvParams& P, const float* in, float* tmp, float* out, cudaStream_t st) {
+    if (try_fused(P, in, out, st)) return 1;
+    // generic radii: two passes through an intermediate cube
     const int XW = kXC + 2 * P.rp;
     const size_t smem = (size_t)XW * (kLC + 2 * P.rl + kLC) * sizeof(float);
     static bool attr_done = false;
