@@ -204,6 +204,77 @@ rubix_status rubix_cube_stats(rubix_cube_t *h, int64_t *stats, int32_t *n_inout)
 rubix_status rubix_spaxel_sort_noalloc(const rubix_particles *p, const rubix_telescope *tel,
                                        int32_t *perm_out, int32_t *seg_off_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: many galaxies through one resident SSP grid.
+ *
+ * The paper motivates fast forward modelling for large simulation suites and
+ * inference loops (Sec. 1, Sec. 6) but defines no server; this is the
+ * library's request interface for that use. A server owns one device copy of
+ * the SSP grid, tiled for one output wavelength grid, and a host thread that
+ * runs a continuous-batching loop:
+ *   - admission: a request is admitted when a slot is free and its device
+ *     footprint (every scratch and cube buffer of its forward model) fits in
+ *     hbm_budget_bytes next to the requests already on the GPU; the queue is
+ *     FIFO, so a large request is never starved by smaller ones behind it;
+ *   - each admitted request stages, assigns, sorts and sets up its particles
+ *     on its own stream while earlier requests deposit;
+ *   - requests whose setup is enqueued are deposited together: one deposit
+ *     launch covers up to max_batch galaxies (<= 64) of different particle
+ *     counts and cube sizes, sharing each shared-memory template slab;
+ *   - the combine, PSF, LSF and noise of each request then run on its stream.
+ * The work decomposition of a request never depends on the others, so its
+ * cube is bitwise the same alone, in any mix, and from rubix_cube_forward.
+ * Device memory comes from a stream-ordered pool owned by the server, so the
+ * loop never synchronises the device.
+ * ------------------------------------------------------------------------- */
+
+/* Create a server on the current device. wavelength_grid gives the output
+ * wavelength grid every request must use (n_lambda, lambda0, dlambda,
+ * z_cosmo are read). hbm_budget_bytes bounds the summed footprints of the
+ * admitted requests (the SSP grid is outside it). max_slots (1..256): requests
+ * on the GPU at once. max_batch (1..64): galaxies per deposit launch; 1 gives
+ * one galaxy per launch. */
+rubix_status rubix_serve_create(const rubix_ssp_grid *ssp, const rubix_telescope *wavelength_grid,
+                                size_t hbm_budget_bytes, int32_t max_slots, int32_t max_batch,
+                                rubix_server_t **out);
+
+/* Queue one forward model; returns at once with a ticket. Particle arrays and
+ * cube_out (float32 [ny][nx][n_lambda], device if cube_on_device else host)
+ * belong to the caller and must stay valid until the request is finished.
+ * Host particle arrays are copied when the request is admitted; device ones
+ * are read in place. noise_seed / noise_s2n as in rubix_cube_forward.
+ * RUBIX_ERR_REJECTED: the request's footprint alone exceeds the budget.
+ * RUBIX_ERR_INVALID_ARG: bad arguments, or a wavelength grid other than the
+ * server's. */
+rubix_status rubix_serve_submit(rubix_server_t *srv, const rubix_telescope *tel, const rubix_particles *p,
+                                uint64_t noise_seed, float noise_s2n, float *cube_out, int32_t cube_on_device,
+                                uint64_t *ticket);
+
+/* Status of a request without waiting: RUBIX_OK (finished; latency_s, if not
+ * NULL, gets submit-to-completion seconds), RUBIX_ERR_NOT_READY (queued or on
+ * the GPU), or the error that ended it (RUBIX_ERR_CANCELLED, ..._OOM, ...).
+ * An unknown ticket gives RUBIX_ERR_INVALID_ARG. */
+rubix_status rubix_serve_poll(rubix_server_t *srv, uint64_t ticket, double *latency_s);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request; returns as
+ * rubix_serve_poll, with RUBIX_ERR_TIMEOUT if the time ran out first. */
+rubix_status rubix_serve_wait(rubix_server_t *srv, uint64_t ticket, double timeout_s);
+
+/* Cancel a queued request: RUBIX_OK, and it will never touch its buffers.
+ * A request already on the GPU cannot be cancelled: RUBIX_ERR_NOT_READY (it
+ * completes normally). A finished request returns its final status. */
+rubix_status rubix_serve_cancel(rubix_server_t *srv, uint64_t ticket);
+
+/* Server counters: [0] submitted, [1] finished OK, [2] rejected, [3] cancelled,
+ * [4] failed, [5] deposit launches, [6] largest batch, [7] device bytes in use
+ * by admitted requests, [8] peak of [7], [9] requests on the GPU now,
+ * [10] queued now. n_inout: capacity in, number written out. */
+rubix_status rubix_serve_stats(rubix_server_t *srv, int64_t *stats, int32_t *n_inout);
+
+/* Finish every admitted request, cancel the queued ones, stop the loop and
+ * free the server. */
+rubix_status rubix_serve_destroy(rubix_server_t *srv);
+
 /* Thread-local message for the last non-OK status returned on this thread. */
 const char *rubix_last_error_message(void);
 

@@ -145,7 +145,8 @@ int launch_items(const ItemParams& P, cudaStream_t st) {
 // ----------------------------------------------------------------------------
 // K4: deposit.
 // ----------------------------------------------------------------------------
-constexpr int kDepHeader = 128;  // mbarrier + counters; the slab starts 128-B aligned
+// kDepHeader (kernels.h): mbarrier, counters and the job work table; the slab
+// starts 1024-B aligned after it.
 
 size_t deposit_smem_bytes(int n_rows_alloc, int slab_w, int elem_bytes) {
     return kDepHeader + (size_t)n_rows_alloc * slab_w * elem_bytes;
@@ -307,22 +308,52 @@ __device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g
     for (int i = 0; i < R; ++i) acc[i] += bin_value<T>(w4, g4, C, C.j0 + 31 * i + lane, lane, use_slab, slab, tpl);
 }
 
+// Per-tile cost of each job (in-field particles + cost_c0 per work item) and
+// its exclusive prefix, read from the device-side counts of every job.
+__global__ void k_job_cost(const DepositParams P, long long* job_cost) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    long long acc = 0;
+    for (int j = 0; j < P.n_jobs; ++j) {
+        const DepJob& J = P.jobs[j];
+        job_cost[j] = acc;
+        const long long n_in = J.seg_off[(long long)J.n_s * P.n_bands];
+        const long long n_items = J.item_off[J.n_s];
+        acc += n_in + (long long)P.cost_c0 * n_items;
+    }
+    job_cost[P.n_jobs] = acc;
+}
+
+// first index i in [0, n] with v[i] > x  (v non-decreasing)
+__device__ __forceinline__ int upper_bound_ll(const long long* __restrict__ v, int n, long long x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (v[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+constexpr int kJobChunk = 32;  // jobs per shared-memory work table
+
 template <typename T, int R>
-__global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const DepositParams P,
+__global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_constant__ DepositParams P,
                                                                    const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int* s_next = reinterpret_cast<int*>(smem + 16);
+    int* s_nv = reinterpret_cast<int*>(smem + 20);         // work items in the current table
+    int* s_job = reinterpret_cast<int*>(smem + 64);        // [kJobChunk] job of table row k
+    int* s_ia = s_job + kJobChunk;                         // [kJobChunk] its first item
+    int* s_pre = s_ia + kJobChunk;                         // [kJobChunk + 1] prefix of item counts
     T* slab = reinterpret_cast<T*>(smem + kDepHeader);
 
     const int lane = threadIdx.x & 31;
     const int nb = P.n_bands;
-    const long long n_in = P.seg_off[(long long)P.n_s * nb];
-    const long long n_items = P.item_off[P.n_s];
+    const long long* __restrict__ jc = P.job_cost;
     const long long C0 = P.cost_c0;
-    const long long Ct = n_in + C0 * n_items;
-    if (Ct <= 0) return;
-    const long long total = Ct * P.n_tiles;
+    const long long CT = jc[P.n_jobs];
+    if (CT <= 0) return;
+    const long long total = CT * P.n_tiles;
     const long long lo = total * blockIdx.x / gridDim.x;
     const long long hi = total * (blockIdx.x + 1) / gridDim.x;
     if (lo >= hi) return;
@@ -334,7 +365,6 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const DepositP
     __syncthreads();
 
     const T* __restrict__ tpl = reinterpret_cast<const T*>(P.ssp.tpl);
-    const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(P.rec);
     TileCtx C;
     C.slab_w = P.slab_w;
     C.da = (P.ssp.n_age > 1) ? P.ssp.n_Z : 0;
@@ -344,20 +374,41 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const DepositP
     C.n_ls = P.ssp.n_ls;
     uint32_t phase = 0;
 
-    for (long long t = lo / Ct; t < P.n_tiles && t * Ct < hi; ++t) {
-        const long long a = max(lo - t * Ct, 0ll), b = min(hi - t * Ct, Ct);
+    for (long long t = lo / CT; t < P.n_tiles && t * CT < hi; ++t) {
+        const long long a = max(lo - t * CT, 0ll), b = min(hi - t * CT, CT);
         if (a >= b) continue;
-        const int i_a = (int)item_lower_bound(P.items, n_items, C0, a);
-        const int i_b = (int)item_lower_bound(P.items, n_items, C0, b);
-        if (i_a >= i_b) continue;
+        // jobs overlapping the CTA's cost range [a, b) of this tile
+        const int ja = upper_bound_ll(jc, P.n_jobs + 1, a) - 1;
+        const int jb = min(upper_bound_ll(jc, P.n_jobs + 1, b - 1), P.n_jobs);
         C.klo = P.tile_klo[t];
         C.j0 = (int)t * P.tile_w;
+
+      for (int cj = ja; cj < jb; cj += kJobChunk) {
+        __syncthreads();  // every warp is done with the previous table
+        if (threadIdx.x == 0) {
+            int nv = 0, k = 0;
+            s_pre[0] = 0;
+            for (int j = cj; j < min(jb, cj + kJobChunk); ++j, ++k) {
+                const DepJob& J = P.jobs[j];
+                const long long ctj = jc[j + 1] - jc[j];
+                const long long aj = max(a - jc[j], 0ll), bj = min(b - jc[j], ctj);
+                const long long n_items = J.item_off[J.n_s];
+                const int ia = (int)item_lower_bound(J.items, n_items, C0, aj);
+                const int ib = (int)item_lower_bound(J.items, n_items, C0, bj);
+                s_job[k] = j;
+                s_ia[k] = ia;
+                nv += max(ib - ia, 0);
+                s_pre[k + 1] = nv;
+            }
+            for (; k < kJobChunk; ++k) s_pre[k + 1] = nv;
+            *s_nv = nv;
+        }
 
         for (int band = 0; band < nb; ++band) {
             C.row0 = P.band_row0[band];
             __syncthreads();  // all warps are done with the previous slab and rows
             if (threadIdx.x == 0) {
-                *s_next = i_a;
+                *s_next = 0;
                 if (C.slab_w > 0) {
                     fence_proxy_async_smem();
                     mbar_arrive_expect_tx(bar, (uint32_t)(P.n_boxes * P.box_rows * C.slab_w * (int)sizeof(T)));
@@ -376,19 +427,24 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const DepositP
                 return;
             }
 
+            const int nv = *s_nv;
             while (true) {
-                int it = 0;
-                if (lane == 0) it = atomicAdd(s_next, 1);
-                it = __shfl_sync(0xffffffffu, it, 0);
-                if (it >= i_b) break;
-                const Item I = P.items[it];
+                int v = 0;
+                if (lane == 0) v = atomicAdd(s_next, 1);
+                v = __shfl_sync(0xffffffffu, v, 0);
+                if (v >= nv) break;
+                int k = 0;
+                while (s_pre[k + 1] <= v) ++k;  // table row holding work item v
+                const DepJob& J = P.jobs[s_job[k]];
+                const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(J.rec);
+                const Item I = J.items[s_ia[k] + (v - s_pre[k])];
                 int qb = I.begin, qe = I.end;
                 if (nb > 1) {
-                    qb = max(qb, P.seg_off[(long long)I.spaxel * nb + band]);
-                    qe = min(qe, P.seg_off[(long long)I.spaxel * nb + band + 1]);
+                    qb = max(qb, J.seg_off[(long long)I.spaxel * nb + band]);
+                    qe = min(qe, J.seg_off[(long long)I.spaxel * nb + band + 1]);
                 }
                 if (band > 0 && qb >= qe) continue;
-                if (I.part_row >= P.part_cap || I.spaxel < 0 || I.spaxel >= P.n_s) {
+                if (I.part_row >= J.part_cap || I.spaxel < 0 || I.spaxel >= J.n_s) {
                     if (lane == 0) atomicOr(P.err, kErrBadItem);
                     continue;
                 }
@@ -418,8 +474,8 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const DepositP
                     }
                     deposit_particle<T, R>(w4, g4, C, slab, tpl, lane, acc, P.slow_count);
                 }
-                float* dst = (I.part_row < 0) ? P.cube + (long long)I.spaxel * P.n_lambda
-                                              : P.partials + (long long)I.part_row * P.n_lambda;
+                float* dst = (I.part_row < 0) ? J.cube + (long long)I.spaxel * P.n_lambda
+                                              : J.partials + (long long)I.part_row * P.n_lambda;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int j = C.j0 + 31 * r + lane;
@@ -430,6 +486,7 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const DepositP
                 }
             }
         }
+      }
     }
 }
 
@@ -448,8 +505,10 @@ static int launch_deposit_t(const DepositParams& P, const CUtensorMap* tmap, int
         default: return -1;
     }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    if (P.n_jobs < 1 || P.n_jobs > kMaxJobs) return -1;
+    k_job_cost<<<1, 32, 0, st>>>(P, P.job_cost);
     fn<<<n_ctas, threads, smem, st>>>(P, *tmap);
-    return 1;
+    return 2;  // job-cost prep + deposit
 }
 
 int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,

@@ -101,14 +101,26 @@ struct ItemParams {
 };
 int launch_items(const ItemParams& P, cudaStream_t st);
 
-// K4: deposit.
-struct DepositParams {
-    SspDev ssp;
+// K4: deposit. One launch deposits up to kMaxJobs galaxies (jobs) that share
+// the SSP grid and the output wavelength grid.
+constexpr int kMaxJobs = 64;
+constexpr int kDepHeader = 1024;  // deposit shared-memory header (barrier, counters, job table)
+struct DepJob {
     const DepRec* rec;
     const Item* items;
     const int* item_off;     // [n_s + 1]: total items at [n_s]
     const int* seg_off;      // [n_s * n_bands + 2]: in-field particles at [n_s * n_bands]
+    float* cube;             // [n_s][n_lambda]
+    float* partials;         // [part_cap][n_lambda]
+    long long part_cap;
     int n_s;
+    int pad;
+};
+struct DepositParams {
+    SspDev ssp;
+    DepJob jobs[kMaxJobs];
+    int n_jobs;
+    long long* job_cost;     // [n_jobs + 1] device scratch: exclusive prefix of the jobs' per-tile cost
     int n_bands;
     int band_row0[kMaxBands];  // first template row of each band's slab
     int n_lambda;
@@ -118,9 +130,6 @@ struct DepositParams {
     int slab_w;              // nodes per slab row (0 = no slab: global path only)
     int box_rows, n_boxes;   // TMA boxes covering one band's template rows
     int cost_c0;             // per-item cost in particle units
-    float* cube;             // [n_s][n_lambda]
-    float* partials;         // [n_parts][n_lambda]
-    long long part_cap;      // rows of `partials`
     unsigned* err;
     unsigned long long* slow_count;
 };
@@ -143,6 +152,8 @@ struct ConvParams {
     uint32_t seed_lo, seed_hi;
 };
 int launch_psf_lsf(const ConvParams& P, const float* in, float* tmp, float* out, cudaStream_t st);
+// True if launch_psf_lsf needs the intermediate cube `tmp` for these radii.
+bool psf_lsf_needs_tmp(int rp, int rl);
 
 // K7/K8: adjoint.
 struct AdjointParams {

@@ -247,23 +247,28 @@ static bool launch_fused(const ConvParams& P, const float* in, float* out, cudaS
 
 // Radii with a fused instantiation: the PSF of FWHM 1.5 spaxels (rp = 3) and
 // LSFs of sigma 1.2 A on 1.25 A or 3 A bins (rl = 4, 2), plus neighbours.
+#define RUBIX_FUSED_RADII(X) X(3, 4) X(3, 2) X(3, 0) X(0, 4) X(0, 2) X(2, 4) X(4, 4) X(3, 3) X(3, 5)
+
 static bool try_fused(const ConvParams& P, const float* in, float* out, cudaStream_t st) {
 #ifdef RUBIX_PSF_TWO_PASS
     return false;
 #endif
 #define RUBIX_FUSED_CASE(RP_, RL_) \
     if (P.rp == RP_ && P.rl == RL_) return launch_fused<RP_, RL_>(P, in, out, st);
-    RUBIX_FUSED_CASE(3, 4)
-    RUBIX_FUSED_CASE(3, 2)
-    RUBIX_FUSED_CASE(3, 0)
-    RUBIX_FUSED_CASE(0, 4)
-    RUBIX_FUSED_CASE(0, 2)
-    RUBIX_FUSED_CASE(2, 4)
-    RUBIX_FUSED_CASE(4, 4)
-    RUBIX_FUSED_CASE(3, 3)
-    RUBIX_FUSED_CASE(3, 5)
+    RUBIX_FUSED_RADII(RUBIX_FUSED_CASE)
 #undef RUBIX_FUSED_CASE
     return false;
+}
+
+bool psf_lsf_needs_tmp(int rp, int rl) {
+#ifdef RUBIX_PSF_TWO_PASS
+    return true;
+#endif
+#define RUBIX_FUSED_HAS(RP_, RL_) \
+    if (rp == RP_ && rl == RL_) return false;
+    RUBIX_FUSED_RADII(RUBIX_FUSED_HAS)
+#undef RUBIX_FUSED_HAS
+    return true;
 }
 
 int launch_psf_lsf(const ConvParams& P, const float* in, float* tmp, float* out, cudaStream_t st) {
