@@ -250,6 +250,11 @@ rubix_status rubix_serve_submit(rubix_server_t *srv, const rubix_telescope *tel,
                                 uint64_t noise_seed, float noise_s2n, float *cube_out, int32_t cube_on_device,
                                 uint64_t *ticket);
 
+/* Device bytes a request would hold while on the GPU (what admission counts
+ * against hbm_budget_bytes), without submitting it. */
+rubix_status rubix_serve_footprint(rubix_server_t *srv, const rubix_telescope *tel, const rubix_particles *p,
+                                   int32_t cube_on_device, size_t *bytes);
+
 /* Status of a request without waiting: RUBIX_OK (finished; latency_s, if not
  * NULL, gets submit-to-completion seconds), RUBIX_ERR_NOT_READY (queued or on
  * the GPU), or the error that ended it (RUBIX_ERR_CANCELLED, ..._OOM, ...).

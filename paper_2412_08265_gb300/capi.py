@@ -80,6 +80,17 @@ _SIGS = {
     "rubix_cube_stats": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "rubix_spaxel_sort_noalloc": (C.c_int32, [C.POINTER(rubix_particles), C.POINTER(rubix_telescope),
                                               C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rubix_serve_create": (C.c_int32, [C.POINTER(rubix_ssp_grid), C.POINTER(rubix_telescope), C.c_size_t,
+                                       C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
+    "rubix_serve_submit": (C.c_int32, [C.c_void_p, C.POINTER(rubix_telescope), C.POINTER(rubix_particles),
+                                       C.c_uint64, C.c_float, C.c_void_p, C.c_int32, C.POINTER(C.c_uint64)]),
+    "rubix_serve_footprint": (C.c_int32, [C.c_void_p, C.POINTER(rubix_telescope), C.POINTER(rubix_particles),
+                                          C.c_int32, C.POINTER(C.c_size_t)]),
+    "rubix_serve_poll": (C.c_int32, [C.c_void_p, C.c_uint64, C.POINTER(C.c_double)]),
+    "rubix_serve_wait": (C.c_int32, [C.c_void_p, C.c_uint64, C.c_double]),
+    "rubix_serve_cancel": (C.c_int32, [C.c_void_p, C.c_uint64]),
+    "rubix_serve_stats": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "rubix_serve_destroy": (C.c_int32, [C.c_void_p]),
     "rubix_last_error_message": (C.c_char_p, []),
     "rubix_version": (C.c_char_p, []),
 }
@@ -186,6 +197,61 @@ def rubix_spaxel_sort_noalloc(p: rubix_particles, tel: rubix_telescope, perm_out
     fixed array inside the library, so n <= 262144 and nx*ny <= 262143."""
     _call("rubix_spaxel_sort_noalloc", C.byref(p), C.byref(tel), C.c_void_p(perm_out), C.c_void_p(seg_off_out),
           C.c_void_p(stream))
+
+
+def rubix_serve_create(ssp: rubix_ssp_grid, wavelength_grid: rubix_telescope, hbm_budget_bytes: int,
+                       max_slots: int, max_batch: int) -> int:
+    h = C.c_void_p()
+    _call("rubix_serve_create", C.byref(ssp), C.byref(wavelength_grid), C.c_size_t(hbm_budget_bytes),
+          C.c_int32(max_slots), C.c_int32(max_batch), C.byref(h))
+    return h.value
+
+
+def rubix_serve_submit(srv: int, tel: rubix_telescope, p: rubix_particles, noise_seed: int, noise_s2n: float,
+                       cube_out: int, cube_on_device: int) -> int:
+    t = C.c_uint64()
+    _call("rubix_serve_submit", C.c_void_p(srv), C.byref(tel), C.byref(p), C.c_uint64(noise_seed),
+          C.c_float(noise_s2n), C.c_void_p(cube_out), C.c_int32(cube_on_device), C.byref(t))
+    return t.value
+
+
+def rubix_serve_footprint(srv: int, tel: rubix_telescope, p: rubix_particles, cube_on_device: int) -> int:
+    b = C.c_size_t()
+    _call("rubix_serve_footprint", C.c_void_p(srv), C.byref(tel), C.byref(p), C.c_int32(cube_on_device),
+          C.byref(b))
+    return int(b.value)
+
+
+def rubix_serve_poll(srv: int, ticket: int) -> tuple[int, float]:
+    """(status, latency_s): status is RUBIX_OK, RUBIX_ERR_NOT_READY or the request's error."""
+    lat = C.c_double(0.0)
+    st = load().rubix_serve_poll(C.c_void_p(srv), C.c_uint64(ticket), C.byref(lat))
+    return int(st), float(lat.value)
+
+
+def rubix_serve_wait(srv: int, ticket: int, timeout_s: float) -> int:
+    """Status after waiting (RUBIX_ERR_TIMEOUT if the time ran out); does not raise."""
+    return int(load().rubix_serve_wait(C.c_void_p(srv), C.c_uint64(ticket), C.c_double(timeout_s)))
+
+
+def rubix_serve_cancel(srv: int, ticket: int) -> int:
+    return int(load().rubix_serve_cancel(C.c_void_p(srv), C.c_uint64(ticket)))
+
+
+def rubix_serve_stats(srv: int) -> list[int]:
+    buf = (C.c_int64 * 16)()
+    n = C.c_int32(16)
+    _call("rubix_serve_stats", C.c_void_p(srv), buf, C.byref(n))
+    return [int(buf[i]) for i in range(n.value)]
+
+
+def rubix_serve_destroy(srv: int) -> None:
+    _call("rubix_serve_destroy", C.c_void_p(srv))
+
+
+def last_error_message() -> str:
+    m = load().rubix_last_error_message()
+    return m.decode() if m else ""
 
 
 def rubix_version() -> str:

@@ -76,19 +76,6 @@ extern "C" rubix_status rubix_cube_destroy(rubix_cube_t* h) {
     return RUBIX_OK;
 }
 
-static rubix_status check_particles(const rubix_particles* p) {
-    if (!p) return fail(RUBIX_ERR_INVALID_ARG, "particles is NULL");
-    if (p->n < 0 || p->n > (1ll << 30)) return fail(RUBIX_ERR_INVALID_ARG, "n out of range");
-    if (p->n == 0) return RUBIX_OK;
-    if (!p->x || !p->y || !p->mass || !p->age || !p->Z) return fail(RUBIX_ERR_INVALID_ARG, "x, y, mass, age, Z required");
-    if (p->preprojected) {
-        if (!p->v_los) return fail(RUBIX_ERR_INVALID_ARG, "v_los required when preprojected");
-    } else {
-        if (!p->z || !p->vy || !p->vz) return fail(RUBIX_ERR_INVALID_ARG, "z, vy, vz required when not preprojected");
-    }
-    return RUBIX_OK;
-}
-
 static inline void rec_ev(rubix_cube* h, int i, cudaStream_t st) {
     if (h->prof && h->ev) cudaEventRecord(h->ev[i], st);
 }

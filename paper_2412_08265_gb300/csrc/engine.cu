@@ -135,6 +135,19 @@ rubix_status validate_telescope(const rubix_telescope* tel, double ssp_dlambda) 
     return RUBIX_OK;
 }
 
+rubix_status check_particles(const rubix_particles* p) {
+    if (!p) return fail(RUBIX_ERR_INVALID_ARG, "particles is NULL");
+    if (p->n < 0 || p->n > (1ll << 30)) return fail(RUBIX_ERR_INVALID_ARG, "n out of range");
+    if (p->n == 0) return RUBIX_OK;
+    if (!p->x || !p->y || !p->mass || !p->age || !p->Z) return fail(RUBIX_ERR_INVALID_ARG, "x, y, mass, age, Z required");
+    if (p->preprojected) {
+        if (!p->v_los) return fail(RUBIX_ERR_INVALID_ARG, "v_los required when preprojected");
+    } else {
+        if (!p->z || !p->vy || !p->vz) return fail(RUBIX_ERR_INVALID_ARG, "z, vy, vz required when not preprojected");
+    }
+    return RUBIX_OK;
+}
+
 bool same_wavelength_grid(const SspState& S, const rubix_telescope* tel) {
     return tel->n_lambda == S.n_lambda && tel->lambda0 == S.lambda0 && tel->dlambda == S.dlambda &&
            tel->z_cosmo == S.z_cosmo;

@@ -46,6 +46,8 @@ rubix_status validate_telescope(const rubix_telescope* tel, double ssp_dlambda);
 rubix_status ssp_state_create(const rubix_ssp_grid* ssp, const rubix_telescope* wavelength_grid, SspState** out);
 void ssp_state_destroy(SspState* S);
 bool same_wavelength_grid(const SspState& S, const rubix_telescope* tel);
+// Particle descriptor checks shared by every entry point (arrays present, n in range).
+rubix_status check_particles(const rubix_particles* p);
 
 // Where a plan's device buffers come from: cudaMalloc, or stream-ordered
 // allocation on `stream` from `pool` (the server, which must not synchronise).
