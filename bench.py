@@ -186,6 +186,121 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# serving: a Poisson request stream through the continuous-batching server,
+# against the same server restricted to one galaxy per launch and one request
+# on the GPU at a time (sequential one-galaxy-per-launch)
+# ---------------------------------------------------------------------------
+SERVE_SPAXEL_KPC = 0.2
+
+
+def _drive(torch, srv, dev, reqs, ins, arrivals):
+    """Submit request i at arrivals[i] seconds (host clock), poll to completion.
+    Returns per-request latency (arrival -> completion, s) and the makespan."""
+    from paper_2412_08265_gb300 import capi, synth
+    n = len(reqs)
+    lat = np.zeros(n)
+    done_t = np.zeros(n)
+    pend = {}
+    t0 = time.perf_counter() + 0.02
+    i = 0
+    while i < n or pend:
+        now = time.perf_counter()
+        while i < n and now >= t0 + arrivals[i]:
+            tel = synth.serving_telescope(reqs[i]["side"])
+            out = torch.empty((tel.ny, tel.nx, tel.n_lambda), dtype=torch.float32, device=dev)
+            t_sub = time.perf_counter()
+            pend[srv.submit(tel, ins[i], out)] = (i, out, t_sub)
+            i += 1
+            now = time.perf_counter()
+        for tk in list(pend):
+            st, l = srv.poll(tk)
+            if st == capi.RUBIX_ERR_NOT_READY:
+                continue
+            if st != capi.RUBIX_OK:
+                raise RuntimeError(f"request failed with status {st}: {capi.last_error_message()}")
+            j, out, t_sub = pend.pop(tk)
+            done_t[j] = t_sub + l
+            lat[j] = done_t[j] - (t0 + arrivals[j])
+        nxt = (t0 + arrivals[i] - time.perf_counter()) if i < n else 1e9
+        time.sleep(max(0.0, min(nxt, 1e-4)))
+    return lat, float(done_t.max() - (t0 + arrivals[0]))
+
+
+def run_serving(args, dev, ssp):
+    import torch
+    from paper_2412_08265_gb300 import synth
+    from paper_2412_08265_gb300.serve import Server
+    n_req = args.serve_requests
+    reqs = synth.serving_requests(n_req, seed=4, rate_hz=1.0)
+    unit_arrivals = np.array([r["arrival_s"] for r in reqs])  # Poisson at 1 Hz; rescaled below
+    n_max = max(r["n"] for r in reqs)
+    mothers = [synth.disk_3d_device(n_max, 9000 + g, dev) for g in range(4)]
+    ins, dep, vox = [], [], []
+    for i, r in enumerate(reqs):
+        m = mothers[i % len(mothers)]
+        d = {k: v[: r["n"]] for k, v in m.items()}
+        d["preprojected"] = False
+        d["inclination"] = r["inclination"]
+        ins.append(d)
+        # in-field particles (host-side tally for the deposit count; not timed)
+        half = 0.5 * r["side"] * SERVE_SPAXEL_KPC
+        x = d["x"].double()
+        yp = d["y"].double() * math.cos(r["inclination"]) - d["z"].double() * math.sin(r["inclination"])
+        n_in = int(((x >= -half) & (x < half) & (yp >= -half) & (yp < half)).sum())
+        dep.append(n_in * 3721)
+        vox.append(r["side"] ** 2 * 3721)
+    dep, vox = np.array(dep, dtype=np.float64), np.array(vox, dtype=np.float64)
+    torch.cuda.synchronize()
+    wl_grid = synth.serving_telescope(40)
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def server(slots, batch):
+        return Server(ssp, wl_grid, hbm_budget_bytes=budget, max_slots=slots, max_batch=batch, device=dev)
+
+    # warm both configurations (pool growth, first launches)
+    warm = list(range(min(8, n_req)))
+    for cfg in ((1, 1), (args.serve_slots, args.serve_batch)):
+        srv = server(*cfg)
+        _drive(torch, srv, dev, [reqs[j] for j in warm], [ins[j] for j in warm], np.zeros(len(warm)))
+        srv.close()
+
+    # sequential capacity: every request queued at t = 0
+    res = {}
+    for name, cfg in (("sequential", (1, 1)), ("served", (args.serve_slots, args.serve_batch))):
+        srv = server(*cfg)
+        _, mk = _drive(torch, srv, dev, reqs, ins, np.zeros(n_req))
+        st = srv.stats()
+        srv.close()
+        res[name] = {"saturated": {"deposits_per_s": float(dep.sum() / mk), "requests_per_s": n_req / mk,
+                                   "makespan_s": mk, "deposit_launches": st["deposit_launches"],
+                                   "max_batch": st["max_batch"]}}
+    # Poisson arrivals at a fixed rate: args.serve_load x the sequential capacity
+    rate = args.serve_load * res["sequential"]["saturated"]["requests_per_s"]
+    arrivals = unit_arrivals / rate
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for name, cfg in (("sequential", (1, 1)), ("served", (args.serve_slots, args.serve_batch))):
+        srv = server(*cfg)
+        lat, mk = _drive(torch, srv, dev, reqs, ins, arrivals)
+        st = srv.stats()
+        srv.close()
+        res[name]["poisson"] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                                "mean_ms": 1e3 * float(lat.mean()), "max_ms": 1e3 * float(lat.max()),
+                                "deposits_per_s": float(dep.sum() / mk), "requests_per_s": n_req / mk,
+                                "deposit_launches": st["deposit_launches"], "max_batch": st["max_batch"],
+                                "peak_bytes": st["peak_bytes"]}
+    clk = clocks.stop()
+    return {"requests": n_req, "arrival_rate_hz": rate, "load_vs_sequential_capacity": args.serve_load,
+            "particles": "log-uniform [1e4, 2e7] (prefixes of 4 device-drawn 3-D disks)",
+            "cube_side": "uniform [40, 300] spaxels of 0.2 kpc x 3721 bins",
+            "inclination": "uniform [0, 90] deg", "deposits_total": float(dep.sum()),
+            "voxels_total": float(vox.sum()), "max_slots": args.serve_slots, "max_batch": args.serve_batch,
+            "hbm_budget_bytes": budget, "latency": "arrival to completion seen by the client",
+            "clocks": clk, **res}
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -310,6 +425,8 @@ def run_ours(args):
             "clocks": clk, "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "stage_ms_last_step": stage_last}
+    if args.serve_requests > 0:
+        line["serving"] = run_serving(args, dev, wl.ssp)
     print(json.dumps(line), flush=True)
     model.close()
     if ws > 1:
@@ -327,6 +444,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--particles", type=int, default=1_000_000,
                     help="particles of the mid-size galaxy (smaller only for profiler captures)")
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="requests in the serving stream (0 = no serving run)")
+    ap.add_argument("--serve-load", type=float, default=0.9,
+                    help="Poisson arrival rate as a fraction of the sequential path's capacity")
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-batch", type=int, default=16)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -220,7 +220,10 @@ rubix_status rubix_spaxel_sort_noalloc(const rubix_particles *p, const rubix_tel
  *     on its own stream while earlier requests deposit;
  *   - requests whose setup is enqueued are deposited together: one deposit
  *     launch covers up to max_batch galaxies (<= 64) of different particle
- *     counts and cube sizes, sharing each shared-memory template slab;
+ *     counts and cube sizes, sharing each shared-memory template slab; a
+ *     launch takes requests in queue order while its estimated work stays
+ *     within that of its first request (or a floor of about 2e9 deposits), so
+ *     small requests share launches without waiting behind a larger one;
  *   - the combine, PSF, LSF and noise of each request then run on its stream.
  * The work decomposition of a request never depends on the others, so its
  * cube is bitwise the same alone, in any mix, and from rubix_cube_forward.

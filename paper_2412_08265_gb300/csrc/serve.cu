@@ -54,6 +54,7 @@ struct Request {
     float* out = nullptr;
     bool out_dev = false, out_pinned = false;
     size_t bytes = 0;
+    double work = 0;           // estimated GPU work: deposits + kVoxelWork per cube voxel
     Clock::time_point t_submit, t_done;
     ReqState state = kQueued;
     rubix_status status = RUBIX_ERR_NOT_READY;
@@ -66,6 +67,14 @@ struct Request {
 };
 
 using ReqPtr = std::shared_ptr<Request>;
+
+// Batch formation: a request joins the launch being formed while the launch's
+// estimated work stays within max(kBatchWork, work of its first request), so
+// small requests share launches but never wait behind a large one that was
+// queued after them. Work unit: one deposit (particle x wavelength bin); a
+// cube voxel (zero fill, combine, PSF/LSF) costs about kVoxelWork deposits.
+constexpr double kBatchWork = 2e9;
+constexpr double kVoxelWork = 2.0;
 
 struct Batch {
     cudaEvent_t ev = nullptr;
@@ -173,7 +182,11 @@ bool launch_batch(rubix_server* srv) {
             break;
         }
     if (!B) return false;
-    const int n = std::min<int>((int)srv->ready.size(), srv->max_batch);
+    int n = 1;
+    double work = srv->ready[0]->work;
+    const double cap = std::max(kBatchWork, work);
+    while (n < std::min<int>((int)srv->ready.size(), srv->max_batch) && work + srv->ready[n]->work <= cap)
+        work += srv->ready[n++]->work;
     std::vector<ReqPtr> batch(srv->ready.begin(), srv->ready.begin() + n);
     srv->ready.erase(srv->ready.begin(), srv->ready.begin() + n);
     DepJob jobs[kMaxJobs];
@@ -393,6 +406,7 @@ extern "C" rubix_status rubix_serve_submit(rubix_server_t* srv, const rubix_tele
         cudaGetLastError();
     }
     r->bytes = plan_bytes(*srv->S, tel, std::max<int64_t>(p->n, 1), !r->out_dev, false, !p->on_device);
+    r->work = ((double)p->n + kVoxelWork * (double)tel->nx * tel->ny) * tel->n_lambda;
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) return fail(RUBIX_ERR_INVALID_ARG, "server is shutting down");

@@ -19,7 +19,8 @@ generators stand in for them with galaxies and templates of the same shape:
   whose temperatures fall with age, times 20 Gaussian absorption lines whose
   depths vary smoothly with (age, Z).
 
-All generators use numpy's PCG64 with an explicit seed.
+All generators use numpy's PCG64 with an explicit seed, except
+:func:`disk_3d_device`, which draws on a CUDA device with torch's generator.
 """
 from __future__ import annotations
 
@@ -323,3 +324,28 @@ def serving_requests(n_requests: int, seed: int = 4, n_min: float = 1e4, n_max: 
 def serving_telescope(side: int) -> Telescope:
     return Telescope(nx=side, ny=side, spaxel_size=0.2, n_lambda=3721, lambda0=4750.0,
                      dlambda=1.25)
+
+
+def disk_3d_device(n: int, seed: int, device, r_scale: float = 3.0, h_scale: float = 0.3,
+                   v_circ: float = 200.0, r_turn: float = 2.0, sigma_v: float = 50.0) -> dict:
+    """The distributions of :func:`disk_3d`, drawn on a CUDA device with torch's
+    Philox generator (for request streams too large to draw on the host).
+    Returns a dict of float32 device tensors x, y, z, vx, vy, vz, mass, age, Z;
+    a prefix of length m is itself a sample of m particles."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f = dict(device=device, dtype=torch.float32, generator=g)
+    u = lambda: torch.rand(n, **f).clamp_min_(1e-12)
+    R = -r_scale * (torch.log(u()) + torch.log(u()))  # Gamma(2, r_scale)
+    phi = (2.0 * math.pi) * torch.rand(n, **f)
+    s = torch.rand(n, **f) - 0.5                        # Laplace(0, h_scale) by inversion
+    zz = -h_scale * torch.sign(s) * torch.log1p(-2.0 * s.abs()).clamp_max(0.0)
+    vphi = v_circ * torch.tanh(R / r_turn)
+    vx = -vphi * torch.sin(phi) + sigma_v * torch.randn(n, **f)
+    vy = vphi * torch.cos(phi) + sigma_v * torch.randn(n, **f)
+    vz = sigma_v * torch.randn(n, **f)
+    age = torch.exp(math.log(0.1) + (math.log(13.5) - math.log(0.1)) * torch.rand(n, **f))
+    Z = torch.exp(math.log(1e-4) + (math.log(0.04) - math.log(1e-4)) * torch.rand(n, **f))
+    mass = torch.exp(math.log(1e5) + 0.5 * torch.randn(n, **f))
+    return dict(x=R * torch.cos(phi), y=R * torch.sin(phi), z=zz, vx=vx, vy=vy, vz=vz, mass=mass, age=age, Z=Z)
