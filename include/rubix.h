@@ -68,7 +68,8 @@ typedef int32_t rubix_status;
 #define RUBIX_BF16 1
 #define RUBIX_F16 2
 
-/* SSP library (Sec. 3: "a lookup from a simple stellar population library").
+/* SSP library (Sec. 3: star spectra are looked up in a simple stellar
+ * population library).
  * All pointers are HOST pointers, read during rubix_cube_create only. */
 typedef struct rubix_ssp_grid {
     int32_t n_age, n_Z, n_lambda;   /* grid sizes, each >= 1; n_lambda >= 2 */
@@ -79,8 +80,8 @@ typedef struct rubix_ssp_grid {
     int32_t storage_dtype;          /* RUBIX_F32 | RUBIX_BF16 | RUBIX_F16 */
 } rubix_ssp_grid;
 
-/* Telescope / IFU (Sec. 3: "accounting for telescope-specific configurations";
- * Sec. 4: Gaussian PSF and LSF). */
+/* Telescope / IFU (Sec. 3: the instrument's spatial and spectral grids and its
+ * responses; Sec. 4: Gaussian PSF and LSF). */
 typedef struct rubix_telescope {
     int32_t nx, ny;                 /* spaxels, each >= 1, nx*ny < 2^24 */
     double spaxel_size;             /* kpc, > 0 */

@@ -31,7 +31,7 @@
 #define OR_C_KMS 299792.458 /* speed of light, km/s */
 
 /* ---------------------------------------------------------------------- */
-/* a1: orientation (Sec. 3, "orientate the galaxy in the field of view").  */
+/* a1: orientation (Sec. 3: the galaxy is rotated into the field of view). */
 /* Reading: rotation about the x axis by the inclination i; the line of    */
 /* sight is the rotated z axis.                                            */
 /*   x' = x,  y' = y cos i - z sin i,  v_los = vy sin i + vz cos i.        */
@@ -61,8 +61,8 @@ int or_orient(int64_t n, const float *x, const float *y, const float *z,
 }
 
 /* ---------------------------------------------------------------------- */
-/* a2: spaxel assignment (Sec. 3, "particles are assigned to the IFU       */
-/* spaxels"). Reading: a square grid of nx*ny spaxels of side `size`,      */
+/* a2: spaxel assignment (Sec. 3: each particle goes to one IFU spaxel).  */
+/* Reading: a square grid of nx*ny spaxels of side `size`,                 */
 /* centred on the origin; spaxel (ix, iy) is the half-open square          */
 /* [x_lo + ix*size, x_lo + (ix+1)*size) x [...). Key = iy*nx + ix; a       */
 /* particle outside the field (or NaN) gets key nx*ny and is dropped.      */
@@ -105,8 +105,8 @@ int or_stable_sort(int64_t n, const int32_t *key, int32_t n_keys, int32_t *perm,
 }
 
 /* ---------------------------------------------------------------------- */
-/* a4: SSP lookup (Sec. 3, "a lookup from a simple stellar population      */
-/* library"). Reading: bilinear interpolation in (log10 age, log10 Z)      */
+/* a4: SSP lookup (Sec. 3: a star's spectrum comes from an SSP library by */
+/* age and metallicity). Reading: bilinear in (log10 age, log10 Z)         */
 /* between the four templates around the particle; outside the node range  */
 /* the coordinate is clamped to the end node. The cell is the half-open    */
 /* interval [node_i, node_i+1) holding the coordinate.                     */
@@ -223,8 +223,8 @@ int or_particle_spectrum(const or_ssp *S, const or_tel *T, double mass, double a
 }
 
 /* ---------------------------------------------------------------------- */
-/* a6: per-spaxel sum (Sec. 3, "the stellar spectra in each spaxel are     */
-/* summed up"):  cube0[s][j] = sum over particles p with key_p = s, in     */
+/* a6: per-spaxel sum (Sec. 3: the spectra of a spaxel's stars are added) */
+/*  cube0[s][j] = sum over particles p with key_p = s, in                  */
 /* increasing p, of S_p(j).  Only spaxels with mask[s] != 0 are computed   */
 /* (mask may be NULL = all); the others are left at zero.                  */
 /* ---------------------------------------------------------------------- */
@@ -305,7 +305,8 @@ int or_deposit(int64_t n, const int32_t *key, const double *v, const float *mass
 }
 
 /* ---------------------------------------------------------------------- */
-/* a7/a8: Gaussian PSF and LSF (Sec. 4: "a Gaussian PSF and LSF").         */
+/* a7/a8: Gaussian PSF and LSF (Sec. 4: both instrument responses are     */
+/* Gaussian).                                                              */
 /* Reading: a discrete kernel sampled at integer offsets d, |d| <= r,      */
 /* g(d) proportional to exp(-d^2 / (2 sigma^2)), normalised to sum 1; PSF  */
 /* sigma = FWHM / (2 sqrt(2 ln 2)) spaxels and 2-D kernel g(dy) g(dx); LSF */

@@ -1,5 +1,5 @@
-// adjoint.cu -- gradients through the pipeline (Abstract and Sec. 1: "compute
-// gradients ... through the entire pipeline"), written by hand instead of by
+// adjoint.cu -- gradients through the pipeline (Abstract and Sec. 1: the
+// forward model is differentiable end to end), written by hand instead of by
 // autodiff.
 //
 // Given G0 = dL/d(cube before PSF/LSF) (the caller of these kernels forms it

@@ -161,7 +161,7 @@ __device__ __forceinline__ int age_band(int ia, int apb, int n_bands) {
 // term j*a_lo is rounded.
 struct __align__(16) DepRec {
     float w[4];        // mass * flux_scale * bilinear weights: (ia,iz) (ia+1,iz) (ia,iz+1) (ia+1,iz+1)
-    int c0_bi;         // (template row of corner (ia,iz)) << 16 | (floor(t(0)) & 0xffff)
+    int c0_bi;         // (SSP cell ia * max(n_Z - 1, 1) + iz) << 16 | (floor(t(0)) & 0xffff)
     float bf;          // t(0) - floor(t(0)), in [0, 1)
     float a_hi;        // dt/dj, high part
     float a_lo;        // dt/dj, low part

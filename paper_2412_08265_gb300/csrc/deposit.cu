@@ -1,33 +1,38 @@
 // deposit.cu -- SSP lookup, Doppler shift, resampling and per-spaxel sum
-// (Sec. 3: "Each star spectrum is calculated as a lookup from a simple stellar
-// population (SSP) library ... Doppler shifted ... resampling ... the stellar
-// spectra in each spaxel are summed up").
+// (Sec. 3: every star's spectrum is taken from an SSP library by age and
+// metallicity, shifted by its line-of-sight velocity, resampled onto the
+// instrument's wavelength grid and added to the spaxel it falls in).
 //
 // K3 (k_setup) turns each in-field particle, in sorted order, into a 32-byte
-// record: its four mass-scaled bilinear corner weights, the template row of
-// the (ia, iz) corner and the affine map t(j) = B + jA from output bin j to
-// the fractional SSP node position.
+// record: its four mass-scaled bilinear corner weights, its SSP cell (the
+// (ia, iz) cell whose four corner templates it interpolates) and the affine
+// map t(j) = B + jA from output bin j to the fractional SSP node position.
+//
+// The templates are kept, for the deposit, as cell quads: for SSP cell c and
+// node k, the float4 of its four corner templates at k, stored node-major
+// ([node][cell]) so that one 2-D TMA box holds a run of consecutive cells (an
+// age band) over a run of nodes.
 //
 // K4 (k_deposit) is persistent: each CTA owns a contiguous, cost-balanced range
 // of (wavelength tile, work item) pairs, a work item being <= chunk particles
-// of one spaxel. For each tile the CTA stages SSP slabs in shared memory with
-// TMA -- all templates of one age band x the tile's node range plus a Doppler
-// halo (TMA's zero fill outside the SSP range is the template's zero
-// extension) -- and its warps accumulate whole items in registers in a fixed
-// particle order. Particles are sorted by (spaxel, age band), so for band b
-// each item's band-b particles are contiguous; band 0 writes the item's row
-// and later bands add to it, in band order.
+// of one spaxel. For each tile and age band the CTA stages the band's quads
+// over the tile's node range plus a Doppler halo in shared memory with TMA
+// (TMA's zero fill outside the SSP range is the template's zero extension),
+// and its warps accumulate whole items in registers in a fixed particle
+// order. Particles are sorted by (spaxel, age band), so for band b each
+// item's band-b particles are contiguous; band 0 writes the item's row and
+// later bands add to it, in band order.
 //
 // Inner loop (one warp per particle, R rounds of 31 consecutive bins; lane l
 // owns bin j0 + 31 r + l): with dt/dj = A in (1 - 1/31, 1] and the round's
 // first bin at node position K0 + phi0, bin l sits at K0 + l + g with
-// g = phi0 - l (1 - A) in (-1, 1). Lane l forms the mass-weighted
-// interpolated template M = sum_c W_c T_c[K0 + l] (4 shared-memory loads at
-// consecutive addresses across the warp: no bank conflicts) and takes the
-// neighbouring node's M from lane l - 1 or l + 1 with one shuffle; the bin
-// value is M + g (M_next - M) or M + g (M - M_prev). Lane 31 only supplies
-// node K0 + 31. Other dt/dj, or Doppler shifts beyond the slab's halo, take a
-// per-bin path.
+// g = phi0 - l (1 - A) in (-1, 1). Lane l reads the quad at node K0 + l (one
+// 16-byte shared load; an odd number of cells per node keeps the warp's 32
+// loads free of bank conflicts), forms the mass-weighted template
+// M = sum_c W_c T_c[K0 + l], and takes the neighbouring node's M from lane
+// l - 1 or l + 1 with one shuffle; the bin value is M + |g| (M_neighbour - M).
+// Lane 31 only supplies node K0 + 31. Other dt/dj, or Doppler shifts beyond
+// the slab's halo, take a per-bin path.
 //
 // Spaxels with more than `chunk` particles are split into several items whose
 // FP32 partial rows K5 adds in FP64 in item order, so the cube is bitwise
@@ -59,7 +64,7 @@ __global__ void k_setup(SetupParams P) {
         r.w[1] = ms * (ta * (1.f - tz));
         r.w[2] = ms * ((1.f - ta) * tz);
         r.w[3] = ms * (ta * tz);
-        const int c0 = ia * P.ssp.n_Z + iz;
+        const int c0 = ia * max(P.ssp.n_Z - 1, 1) + iz;  // SSP cell of the four corners
         // t(j) = ((l0 + j dl) / dop - ls0) / dls = B + j A   (FP64)
         const double dop = (1.0 + P.z_cosmo) * (1.0 + v / kC_kms);
         const double alpha = 1.0 / (dop * P.ssp.dls);
@@ -145,12 +150,12 @@ int launch_items(const ItemParams& P, cudaStream_t st) {
 // ----------------------------------------------------------------------------
 // K4: deposit.
 // ----------------------------------------------------------------------------
-// kDepHeader (kernels.h): mbarrier, counters and the job work table; the slab
-// starts 1024-B aligned after it.
+// Shared memory: kDepHeader bytes (mbarrier, counters, job work table), then
+// the slab: slab_w nodes x ncb cells of quads, node-major (quad of cell c at
+// node k at slab[(k - klo) * ncb + c - cell0]). ncb is odd, so the 16-byte
+// quads that 32 lanes read at consecutive nodes fall in distinct bank groups.
 
-size_t deposit_smem_bytes(int n_rows_alloc, int slab_w, int elem_bytes) {
-    return kDepHeader + (size_t)n_rows_alloc * slab_w * elem_bytes;
-}
+size_t deposit_smem_bytes(int ncb, int slab_w) { return kDepHeader + (size_t)ncb * slab_w * sizeof(float4); }
 
 // First item index i in [0, n] with items[i].begin + c0 * i >= x (item n is
 // the virtual end).
@@ -163,11 +168,6 @@ __device__ __forceinline__ long long item_lower_bound(const Item* __restrict__ i
         if (pre < x) lo = mid + 1; else hi = mid;
     }
     return lo;
-}
-
-template <typename T>
-__device__ __forceinline__ float tpl_global(const T* __restrict__ tpl, int pitch, int n_ls, int row, int k) {
-    return (k >= 0 && k < n_ls) ? TplTraits<T>::ld(tpl + (long long)row * pitch + k) : 0.f;
 }
 
 // Node position of output bin j: t(j) = K + phi, phi in [0, 1). j*a_hi is
@@ -183,129 +183,105 @@ __device__ __forceinline__ int node_pos(int j, int bi, float bf, float a_hi, flo
 }
 
 struct TileCtx {
-    int j0, klo, slab_w, row0, da, dz, n_lambda, pitch, n_ls;
+    int j0, klo, slab_w, ncb, cell0, n_lambda, n_ls, n_cells;
 };
 
+// Quad of `cell` at node k from the global quad array (zero outside the
+// template range: the template's zero extension).
+__device__ __forceinline__ float4 quad_global(const float4* __restrict__ quad, int n_cells, int n_ls, int cell, int k) {
+    return (k >= 0 && k < n_ls) ? __ldg(quad + (long long)k * n_cells + cell) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Mass-weighted bilinear template value at one node: sum_c w_c q_c.
+__device__ __forceinline__ float quad_dot(const float4 w, const float4 q) {
+    float2 p = __fmul2_rn(make_float2(w.x, w.y), make_float2(q.x, q.y));
+    p = __ffma2_rn(make_float2(w.z, w.w), make_float2(q.z, q.w), p);
+    return p.x + p.y;
+}
+
 // Per-bin evaluation for the general path: does bin j's node pair lie in the slab?
-__device__ __noinline__ bool bin_in_slab(const float4 w4, const float4 g4, const TileCtx C, int j, int lane) {
+__device__ __noinline__ bool bin_in_slab(const float4 g4, const TileCtx C, int j, int lane) {
     if (lane == 31 || j >= C.n_lambda) return true;
     const int c0_bi = __float_as_int(g4.x);
+    if ((unsigned)(rec_c0(c0_bi) - C.cell0) >= (unsigned)C.ncb) return false;
     float f;
     const int k = node_pos(j, rec_bi(c0_bi), g4.y, g4.z, g4.w, f) - C.klo;
     return k >= 0 && k + 1 < C.slab_w;
 }
 
 // Spectrum value of one particle at bin j (0 for lane 31 and bins past the end),
-// templates from the slab or, with use_slab false, from global memory.
-template <typename T>
+// quads from the slab or, with use_slab false, from global memory.
 __device__ __noinline__ float bin_value(const float4 w4, const float4 g4, const TileCtx C, int j, int lane,
-                                        bool use_slab, const T* __restrict__ slab, const T* __restrict__ tpl) {
+                                        bool use_slab, const float4* __restrict__ slab,
+                                        const float4* __restrict__ quad) {
     if (lane == 31 || j >= C.n_lambda) return 0.f;
     const int c0_bi = __float_as_int(g4.x);
-    const int c0 = rec_c0(c0_bi);
+    const int cell = rec_c0(c0_bi);
     float f;
     const int k = node_pos(j, rec_bi(c0_bi), g4.y, g4.z, g4.w, f);
-    const int rows[4] = {c0, c0 + C.da, c0 + C.dz, c0 + C.da + C.dz};
-    const float ws[4] = {w4.x, w4.y, w4.z, w4.w};
-    float m0 = 0.f, m1 = 0.f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        if (use_slab) {
-            const T* p = slab + (rows[c] - C.row0) * C.slab_w + (k - C.klo);
-            m0 = fmaf(ws[c], TplTraits<T>::ld(p), m0);
-            m1 = fmaf(ws[c], TplTraits<T>::ld(p + 1), m1);
-        } else {
-            m0 = fmaf(ws[c], tpl_global(tpl, C.pitch, C.n_ls, rows[c], k), m0);
-            m1 = fmaf(ws[c], tpl_global(tpl, C.pitch, C.n_ls, rows[c], k + 1), m1);
-        }
+    float4 q0, q1;
+    if (use_slab) {
+        const float4* p = slab + (k - C.klo) * C.ncb + (cell - C.cell0);
+        q0 = p[0];
+        q1 = p[C.ncb];
+    } else {
+        q0 = quad_global(quad, C.n_cells, C.n_ls, cell, k);
+        q1 = quad_global(quad, C.n_cells, C.n_ls, cell, k + 1);
     }
+    const float m0 = quad_dot(w4, q0), m1 = quad_dot(w4, q1);
     return fmaf(f, m1 - m0, m0);
 }
 
 // Adds one particle's spectrum to acc: acc[r] of lane l (l < 31) is output bin
 // j0 + 31 r + l.
-template <typename T, int R>
+template <int R>
 __device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g4, const TileCtx& C,
-                                                 const T* __restrict__ slab, const T* __restrict__ tpl, int lane,
-                                                 float (&acc)[R], unsigned long long* slow_count) {
+                                                 const float4* __restrict__ slab, const float4* __restrict__ quad,
+                                                 int lane, float lanef, float (&acc)[R],
+                                                 unsigned long long* slow_count) {
     const int c0_bi = __float_as_int(g4.x);
-    const int c0 = rec_c0(c0_bi), bi = rec_bi(c0_bi);
-    const float bf = g4.y, a_hi = g4.z, a_lo = g4.w;
-    float phi0;
-    int K0 = node_pos(C.j0, bi, bf, a_hi, a_lo, phi0);  // node position of the round's first bin
-    const float delta = (1.f - a_hi) - a_lo;            // 1 - dt/dj (exact up to one rounding)
+    const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
+    float f;
+    const int K0 = node_pos(C.j0, bi, g4.y, g4.z, g4.w, f);  // node position of the tile's first bin
+    const float delta = (1.f - g4.z) - g4.w;                 // 1 - dt/dj (exact up to one rounding)
     const int kw = K0 - C.klo;
-    // fast path (warp-uniform test): dt/dj in (1 - 1/31, 1] and every node the
-    // rounds read, K0 .. K0 + 31 R, inside the slab
-    if (C.slab_w > 0 && delta >= 0.f && delta * 31.f < 1.f && kw >= 0 && kw + 31 * R < C.slab_w) {
-        const float ldel = (float)lane * delta;
+    const int cr = cell - C.cell0;
+    // fast path (warp-uniform test): dt/dj in (1 - 1/31, 1], a cell of this
+    // band, and every node the rounds read, K0 .. K0 + 31 R, inside the slab
+    if (delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R) &&
+        (unsigned)cr < (unsigned)C.ncb) {
+        // round r: lane l reads node K0 + o_r + l, o_r = 31 r - (carries so far)
+        const float4* q = slab + (kw + lane) * C.ncb + cr;
+        const int s31 = 31 * C.ncb, s30 = 30 * C.ncb;
+        const float nld = -lanef * delta;
         const float d31 = 31.f * delta;
-        const T* p00 = slab + (c0 - C.row0) * C.slab_w + kw + lane;
-        const T* p10 = p00 + C.da * C.slab_w;
-        const int oz = C.dz * C.slab_w;
-        // round r starts at node K0 + off[r] with fraction ph[r] (t advances by
-        // 31 dt/dj = 31 - 31 delta per round); warp-uniform, computed up front
-        int off[R];
-        float ph[R];
-        {
-            float f = phi0;
-            int o = 0;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                off[r] = o;
-                ph[r] = f;
-                f -= d31;
-                const bool carry = f < 0.f;
-                f = carry ? f + 1.f : f;
-                o += carry ? 30 : 31;
-            }
-        }
-        const float2 wx = make_float2(w4.x, w4.x), wy = make_float2(w4.y, w4.y);
-        const float2 wz = make_float2(w4.z, w4.z), ww = make_float2(w4.w, w4.w);
-        const float2 nl = make_float2(-ldel, -ldel);
-#pragma unroll
-        for (int r = 0; r < R; r += 2) {
-            if (r + 1 < R) {
-                // two rounds at once in packed FP32x2: M at node K0 + off + lane
-                const int o0 = off[r], o1 = off[r + 1];
-                float2 M = __fmul2_rn(wx, make_float2(TplTraits<T>::ld(p00 + o0), TplTraits<T>::ld(p00 + o1)));
-                M = __ffma2_rn(wy, make_float2(TplTraits<T>::ld(p10 + o0), TplTraits<T>::ld(p10 + o1)), M);
-                M = __ffma2_rn(wz, make_float2(TplTraits<T>::ld(p00 + oz + o0), TplTraits<T>::ld(p00 + oz + o1)), M);
-                M = __ffma2_rn(ww, make_float2(TplTraits<T>::ld(p10 + oz + o0), TplTraits<T>::ld(p10 + oz + o1)), M);
-                // bins j0 + 31 r + lane sit at node K0 + off + lane + g, g in (-1, 1);
-                // the neighbour node on g's side comes from lane -+ 1:
-                // value = M + |g| (M_neighbour - M)
-                const float2 g = __fadd2_rn(make_float2(ph[r], ph[r + 1]), nl);
-                float2 X;
-                X.x = __shfl_sync(0xffffffffu, M.x, g.x < 0.f ? lane - 1 : lane + 1);
-                X.y = __shfl_sync(0xffffffffu, M.y, g.y < 0.f ? lane - 1 : lane + 1);
-                const float2 D = __fadd2_rn(X, make_float2(-M.x, -M.y));
-                float2 a = __fadd2_rn(make_float2(acc[r], acc[r + 1]), M);
-                a = __ffma2_rn(make_float2(fabsf(g.x), fabsf(g.y)), D, a);
-                acc[r] = a.x;
-                acc[r + 1] = a.y;
-            } else {
-                const int o0 = off[r];
-                float M = w4.x * TplTraits<T>::ld(p00 + o0);
-                M = fmaf(w4.y, TplTraits<T>::ld(p10 + o0), M);
-                M = fmaf(w4.z, TplTraits<T>::ld(p00 + oz + o0), M);
-                M = fmaf(w4.w, TplTraits<T>::ld(p10 + oz + o0), M);
-                const float g = ph[r] - ldel;
-                const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
-                acc[r] += fmaf(fabsf(g), X - M, M);
-            }
+        for (int r = 0; r < R; ++r) {
+            const float M = quad_dot(w4, *q);
+            // bin j0 + 31 r + l sits at node K0 + o_r + l + g, g = f - l delta in
+            // (-1, 1); the neighbour node on g's side is lane l -+ 1's:
+            // value = M + |g| (M_neighbour - M)
+            const float g = f + nld;
+            const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
+            acc[r] += fmaf(fabsf(g), X - M, M);
+            // the next round starts 31 dt/dj = 31 - 31 delta nodes further on
+            f -= d31;
+            const bool carry = f < 0.f;
+            f = carry ? f + 1.f : f;
+            q += carry ? s30 : s31;
         }
         return;
     }
-    // general path (out of line, rare on the workloads here): each bin's node
-    // pair from the slab if every bin of the warp is inside it, else from global
-    bool ok = C.slab_w > 0;
+    // general path (out of line; rare on the workloads here): each bin's node
+    // pair from the slab if every bin of the warp is inside it, else from the
+    // global quad array
+    bool ok = true;
 #pragma unroll
-    for (int i = 0; i < R; ++i) ok = ok && bin_in_slab(w4, g4, C, C.j0 + 31 * i + lane, lane);
-    const bool use_slab = __all_sync(0xffffffffu, ok);
+    for (int i = 0; i < R; ++i) ok = ok && bin_in_slab(g4, C, C.j0 + 31 * i + lane, lane);
+    const bool use_slab = C.slab_w > 0 && __all_sync(0xffffffffu, ok);
     if (!use_slab && lane == 0 && slow_count) atomicAdd(slow_count, 1ull);
 #pragma unroll
-    for (int i = 0; i < R; ++i) acc[i] += bin_value<T>(w4, g4, C, C.j0 + 31 * i + lane, lane, use_slab, slab, tpl);
+    for (int i = 0; i < R; ++i) acc[i] += bin_value(w4, g4, C, C.j0 + 31 * i + lane, lane, use_slab, slab, quad);
 }
 
 // Per-tile cost of each job (in-field particles + cost_c0 per work item) and
@@ -334,8 +310,12 @@ __device__ __forceinline__ int upper_bound_ll(const long long* __restrict__ v, i
 }
 
 constexpr int kJobChunk = 32;  // jobs per shared-memory work table
+// Work items a warp claims at once (its first lanes look them up together).
+#ifndef RUBIX_DEP_GRAB
+#define RUBIX_DEP_GRAB 4
+#endif
 
-template <typename T, int R>
+template <int R>
 __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_constant__ DepositParams P,
                                                                    const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -345,9 +325,10 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_c
     int* s_job = reinterpret_cast<int*>(smem + 64);        // [kJobChunk] job of table row k
     int* s_ia = s_job + kJobChunk;                         // [kJobChunk] its first item
     int* s_pre = s_ia + kJobChunk;                         // [kJobChunk + 1] prefix of item counts
-    T* slab = reinterpret_cast<T*>(smem + kDepHeader);
+    float4* slab = reinterpret_cast<float4*>(smem + kDepHeader);
 
     const int lane = threadIdx.x & 31;
+    const float lanef = (float)lane;
     const int nb = P.n_bands;
     const long long* __restrict__ jc = P.job_cost;
     const long long C0 = P.cost_c0;
@@ -364,14 +345,13 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_c
     }
     __syncthreads();
 
-    const T* __restrict__ tpl = reinterpret_cast<const T*>(P.ssp.tpl);
     TileCtx C;
     C.slab_w = P.slab_w;
-    C.da = (P.ssp.n_age > 1) ? P.ssp.n_Z : 0;
-    C.dz = (P.ssp.n_Z > 1) ? 1 : 0;
+    C.ncb = P.ncb;
     C.n_lambda = P.n_lambda;
-    C.pitch = P.ssp.pitch;
-    C.n_ls = P.ssp.n_ls;
+    C.n_ls = P.n_ls;
+    C.n_cells = P.n_cells;
+    const uint32_t slab_bytes = (uint32_t)P.n_boxes * (uint32_t)P.box_w * (uint32_t)P.ncb * sizeof(float4);
     uint32_t phase = 0;
 
     for (long long t = lo / CT; t < P.n_tiles && t * CT < hi; ++t) {
@@ -405,16 +385,16 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_c
         }
 
         for (int band = 0; band < nb; ++band) {
-            C.row0 = P.band_row0[band];
+            C.cell0 = P.band_cell0[band];
             __syncthreads();  // all warps are done with the previous slab and rows
             if (threadIdx.x == 0) {
                 *s_next = 0;
                 if (C.slab_w > 0) {
                     fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(bar, (uint32_t)(P.n_boxes * P.box_rows * C.slab_w * (int)sizeof(T)));
+                    mbar_arrive_expect_tx(bar, slab_bytes);
                     for (int bx = 0; bx < P.n_boxes; ++bx)
-                        tma_load_2d(slab + (size_t)bx * P.box_rows * C.slab_w, &tmap, bar, C.klo,
-                                    C.row0 + bx * P.box_rows);
+                        tma_load_2d(slab + (size_t)bx * P.box_w * C.ncb, &tmap, bar, 4 * C.cell0,
+                                    C.klo + bx * P.box_w);
                 }
             }
             bool ok = true;
@@ -428,60 +408,86 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_c
             }
 
             const int nv = *s_nv;
+            constexpr int G = RUBIX_DEP_GRAB;
             while (true) {
-                int v = 0;
-                if (lane == 0) v = atomicAdd(s_next, 1);
-                v = __shfl_sync(0xffffffffu, v, 0);
-                if (v >= nv) break;
-                int k = 0;
-                while (s_pre[k + 1] <= v) ++k;  // table row holding work item v
-                const DepJob& J = P.jobs[s_job[k]];
-                const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(J.rec);
-                const Item I = J.items[s_ia[k] + (v - s_pre[k])];
-                int qb = I.begin, qe = I.end;
-                if (nb > 1) {
-                    qb = max(qb, J.seg_off[(long long)I.spaxel * nb + band]);
-                    qe = min(qe, J.seg_off[(long long)I.spaxel * nb + band + 1]);
-                }
-                if (band > 0 && qb >= qe) continue;
-                if (I.part_row >= J.part_cap || I.spaxel < 0 || I.spaxel >= J.n_s) {
-                    if (lane == 0) atomicOr(P.err, kErrBadItem);
-                    continue;
-                }
-                float acc[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] = 0.f;
-                // records of the next RUBIX_DEP_PREFETCH particles are in flight
-                // while the current one is deposited
-                constexpr int PF = RUBIX_DEP_PREFETCH;
-                float4 wq[PF], gq[PF];
-#pragma unroll
-                for (int k = 0; k < PF; ++k)
-                    if (qb + k < qe) {
-                        wq[k] = rec4[2 * (qb + k)];
-                        gq[k] = rec4[2 * (qb + k) + 1];
+                int v0 = 0;
+                if (lane == 0) v0 = atomicAdd(s_next, G);
+                v0 = __shfl_sync(0xffffffffu, v0, 0);
+                if (v0 >= nv) break;
+                // lanes < G look up one work item each and its band segment
+                int kk = 0, qb = 0, qe = 0, sp = 0, prow = -1;
+                bool live = false;
+                const int v = v0 + lane;
+                if (lane < G && v < nv) {
+                    while (s_pre[kk + 1] <= v) ++kk;  // table row holding work item v
+                    const DepJob& J = P.jobs[s_job[kk]];
+                    const Item I = J.items[s_ia[kk] + (v - s_pre[kk])];
+                    sp = I.spaxel;
+                    prow = I.part_row;
+                    qb = I.begin;
+                    qe = I.end;
+                    if (prow >= J.part_cap || sp < 0 || sp >= J.n_s) {
+                        atomicOr(P.err, kErrBadItem);
+                    } else {
+                        if (nb > 1) {
+                            qb = max(qb, J.seg_off[(long long)sp * nb + band]);
+                            qe = min(qe, J.seg_off[(long long)sp * nb + band + 1]);
+                        }
+                        // band 0 visits every item: it writes the row, zeros included
+                        live = band == 0 || qb < qe;
                     }
-                for (int q = qb; q < qe; ++q) {
-                    const float4 w4 = wq[0], g4 = gq[0];
-#pragma unroll
-                    for (int k = 0; k + 1 < PF; ++k) {
-                        wq[k] = wq[k + 1];
-                        gq[k] = gq[k + 1];
-                    }
-                    if (q + PF < qe) {
-                        wq[PF - 1] = rec4[2 * (q + PF)];
-                        gq[PF - 1] = rec4[2 * (q + PF) + 1];
-                    }
-                    deposit_particle<T, R>(w4, g4, C, slab, tpl, lane, acc, P.slow_count);
                 }
-                float* dst = (I.part_row < 0) ? J.cube + (long long)I.spaxel * P.n_lambda
-                                              : J.partials + (long long)I.part_row * P.n_lambda;
+                unsigned m = __ballot_sync(0xffffffffu, live);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int k = __shfl_sync(0xffffffffu, kk, src);
+                    const int q0 = __shfl_sync(0xffffffffu, qb, src);
+                    const int q1 = __shfl_sync(0xffffffffu, qe, src);
+                    const int s = __shfl_sync(0xffffffffu, sp, src);
+                    const int pr = __shfl_sync(0xffffffffu, prow, src);
+                    const DepJob& J = P.jobs[s_job[k]];
+                    const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(J.rec);
+                    float* dst = (pr < 0) ? J.cube + (long long)s * P.n_lambda
+                                          : J.partials + (long long)pr * P.n_lambda;
+#if !RUBIX_DEP_BANDADD
+                    // later bands add to the row: start moving it into L2 now
+                    if (band > 0 && lane < R && C.j0 + 31 * lane < P.n_lambda)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(dst + C.j0 + 31 * lane));
+#endif
+                    float acc[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int j = C.j0 + 31 * r + lane;
-                    if (lane < 31 && j < P.n_lambda) {
-                        if (band == 0) dst[j] = acc[r];
-                        else dst[j] += acc[r];
+                    for (int r = 0; r < R; ++r) acc[r] = 0.f;
+                    // the next particle's record is in flight while the current one is deposited
+                    float4 wn, gn;
+                    if (q0 < q1) {
+                        wn = rec4[2 * q0];
+                        gn = rec4[2 * q0 + 1];
+                    }
+                    for (int q = q0; q < q1; ++q) {
+                        const float4 w4 = wn, g4 = gn;
+                        if (q + 1 < q1) {
+                            wn = rec4[2 * (q + 1)];
+                            gn = rec4[2 * (q + 1) + 1];
+                        }
+                        deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int j = C.j0 + 31 * r + lane;
+                        if (lane < 31 && j < P.n_lambda) {
+                            if (band == 0) {
+                                dst[j] = acc[r];
+                            } else {
+#if RUBIX_DEP_BANDADD
+                                // one reduction per address and band, bands ordered
+                                // by the CTA barrier: the sum order is fixed
+                                atomicAdd(dst + j, acc[r]);
+#else
+                                dst[j] += acc[r];
+#endif
+                            }
+                        }
                     }
                 }
             }
@@ -490,18 +496,16 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_c
     }
 }
 
-template <typename T>
-static int launch_deposit_t(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,
-                            cudaStream_t st) {
+int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,
+                   cudaStream_t st) {
     if (P.tile_w % 31 != 0) return -1;
     void (*fn)(const DepositParams, const CUtensorMap) = nullptr;
     switch (P.tile_w / 31) {
-        case 1: fn = k_deposit<T, 1>; break;
-        case 2: fn = k_deposit<T, 2>; break;
-        case 3: fn = k_deposit<T, 3>; break;
-        case 4: fn = k_deposit<T, 4>; break;
-        case 5: fn = k_deposit<T, 5>; break;
-        case 6: fn = k_deposit<T, 6>; break;
+#define RUBIX_DEP_R(r) \
+    case r: fn = k_deposit<r>; break;
+        RUBIX_DEP_R(1) RUBIX_DEP_R(2) RUBIX_DEP_R(3) RUBIX_DEP_R(4) RUBIX_DEP_R(5) RUBIX_DEP_R(6)
+        RUBIX_DEP_R(7) RUBIX_DEP_R(8) RUBIX_DEP_R(9) RUBIX_DEP_R(10) RUBIX_DEP_R(11) RUBIX_DEP_R(12)
+#undef RUBIX_DEP_R
         default: return -1;
     }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
@@ -509,16 +513,6 @@ static int launch_deposit_t(const DepositParams& P, const CUtensorMap* tmap, int
     k_job_cost<<<1, 32, 0, st>>>(P, P.job_cost);
     fn<<<n_ctas, threads, smem, st>>>(P, *tmap);
     return 2;  // job-cost prep + deposit
-}
-
-int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,
-                   cudaStream_t st) {
-    switch (P.ssp.dtype) {
-        case 0: return launch_deposit_t<float>(P, tmap, n_ctas, threads, smem, st);
-        case 1: return launch_deposit_t<__nv_bfloat16>(P, tmap, n_ctas, threads, smem, st);
-        case 2: return launch_deposit_t<__half>(P, tmap, n_ctas, threads, smem, st);
-    }
-    return -1;
 }
 
 // ----------------------------------------------------------------------------

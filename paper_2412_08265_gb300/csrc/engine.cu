@@ -161,7 +161,7 @@ void ssp_state_destroy(SspState* S) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(S->device);
-    void* ptrs[] = {S->d_tpl, S->d_la, S->d_lz, S->d_tile_klo, S->d_err, S->d_slow};
+    void* ptrs[] = {S->d_tpl, S->d_quad, S->d_la, S->d_lz, S->d_tile_klo, S->d_err, S->d_slow};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     cudaSetDevice(prev);
@@ -233,81 +233,115 @@ rubix_status ssp_state_create(const rubix_ssp_grid* ssp, const rubix_telescope* 
         S.lz_nodes = h->d_lz;
     }
 
-    // ---- deposit tiling: wavelength tiles and the SSP slab staged per tile ----
-    // The slab holds one age band of templates x (tile nodes + Doppler halo). A
-    // tile is R rounds of 31 bins; choose the fewest bands that give R >= the
-    // minimum (the per-particle setup is shared by R rounds).
+    // ---- cell quads: for SSP cell (ia, iz) and node k, the float4 of its four
+    // bilinear corners (ia,iz) (ia+1,iz) (ia,iz+1) (ia+1,iz+1), in the storage
+    // dtype's values, node-major [n_ls][n_cells] ----
+    h->cz = std::max(S.n_Z - 1, 1);
+    const int ca = std::max(S.n_age - 1, 1);
+    h->n_cells = ca * h->cz;
+    {
+        const int da = (S.n_age > 1) ? 1 : 0, dz = (S.n_Z > 1) ? 1 : 0;
+        auto stored = [&](int ia, int iz, int k) {
+            const float f = (float)ssp->spectra[((size_t)ia * S.n_Z + iz) * S.n_ls + k];
+            if (S.dtype == RUBIX_F32) return f;
+            if (S.dtype == RUBIX_BF16) {
+                const uint32_t u = (uint32_t)f32_to_bf16(f) << 16;
+                float r;
+                std::memcpy(&r, &u, 4);
+                return r;
+            }
+            return __half2float(__float2half_rn(f));
+        };
+        std::vector<float4> q((size_t)S.n_ls * h->n_cells);
+        for (int ia = 0; ia < ca; ++ia)
+            for (int iz = 0; iz < h->cz; ++iz) {
+                const int c = ia * h->cz + iz;
+                for (int k = 0; k < S.n_ls; ++k)
+                    q[(size_t)k * h->n_cells + c] = make_float4(stored(ia, iz, k), stored(ia + da, iz, k),
+                                                                stored(ia, iz + dz, k), stored(ia + da, iz + dz, k));
+            }
+        if (dalloc_sync(&h->d_quad, q.size())) return bail(fail(RUBIX_ERR_OOM, "quad alloc"));
+        if (cudaMemcpy(h->d_quad, q.data(), q.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(RUBIX_ERR_CUDA, "quad copy"));
+    }
+
+    // ---- deposit tiling: wavelength tiles and the quad slab staged per tile
+    // and age band. A band's slab holds ncb cells (odd) x slab_w nodes: the
+    // tile's R rounds of 31 bins plus a Doppler halo of +-RUBIX_DEP_VHALO.
+    // Among the band sizes that fit, take the one with the lowest estimated
+    // cost per particle: n_tiles * (per-particle setup + R rounds + bands). ----
     const double A0 = tel->dlambda / ((1.0 + tel->z_cosmo) * S.dls);
-    const int align = 16 / h->elem;  // TMA: 16-byte aligned innermost coordinate and extent
     const double v_halo = RUBIX_DEP_VHALO;
     const double lam_max = (tel->lambda0 + (tel->n_lambda - 1) * tel->dlambda) / (1.0 + tel->z_cosmo);
-    const double shift = lam_max / S.dls * (v_halo / kC_kms) / (1.0 - v_halo / kC_kms);
-    const int cells = std::max(S.n_age - 1, 1);
-    struct Geo { int bands, apb, box_rows, n_boxes, rows_alloc, R; long long wcap; };
-    Geo best{0, 0, 0, 0, 0, 0, 0}, widest{0, 0, 0, 0, 0, 0, -1};
-    for (int nb = 1; nb <= kMaxBands; ++nb) {
-        if (nb > 1 && S.n_age < 3) break;
-        const int apb = (cells + nb - 1) / nb;
-        if (nb > 1 && (nb - 1) * apb >= cells) continue;  // a band would be empty
-        const int cols = (S.n_age >= 2) ? std::min(apb + 1, S.n_age) : 1;
-        const int rows = cols * S.n_Z;
-        const int n_boxes = (rows + 255) / 256;
-        const int box_rows = ((rows + n_boxes - 1) / n_boxes + 7) / 8 * 8;
-        const int rows_alloc = n_boxes * box_rows;
-        long long wcap = ((long long)h->smem_optin - kDepHeader) / ((long long)rows_alloc * h->elem);
-        wcap = std::min<long long>(wcap, 256);
-        wcap -= wcap % align;
+    const int shift = (int)std::ceil(lam_max / S.dls * (v_halo / kC_kms) / (1.0 - v_halo / kC_kms));
+    const long long budget = (long long)h->smem_optin - kDepHeader;
+    struct Geo { int apb, bands, ncb, box_w, n_boxes, slab_w, R; double cost; };
+    Geo best{0, 0, 0, 0, 0, 0, 0, 1e300};
+    const bool fast_A = A0 <= 1.0 && A0 > 1.0 - 1.0 / 31.0;
+    for (int apb = ca; apb >= 1; --apb) {
+        const int bands = (ca + apb - 1) / apb;
+        if (bands > kMaxBands) break;
+        if (RUBIX_DEP_BANDS > 0 && bands != std::min(RUBIX_DEP_BANDS, ca)) continue;
+        int ncb = apb * h->cz;
+        ncb += (ncb % 2 == 0) ? 1 : 0;
+        if (4 * ncb > 256) continue;  // TMA box: at most 256 elements per dimension
+        const long long wmax = budget / ((long long)ncb * (long long)sizeof(float4));
+        if (wmax < 64) continue;
+        // each box lands 128-byte aligned in shared memory (TMA destination
+        // rule): box_w * ncb * 16 bytes a multiple of 128, i.e. box_w % 8 == 0
+        const int n_boxes = (int)((wmax + 255) / 256);
+        const int box_w = (int)(wmax / n_boxes) / 8 * 8;
+        const int slab_w = n_boxes * box_w;
         int R = 0;
-        for (int r = 6; r >= 1; --r) {
-            const double span = std::max(31.0 * r + 1.0, (31.0 * r - 1.0) * A0 * (1.0 + v_halo / kC_kms) + 2.0);
-            if (span + 2.0 * shift + (align - 1) <= (double)wcap) { R = r; break; }
-        }
-        if (R > best.R) best = Geo{nb, apb, box_rows, n_boxes, rows_alloc, R, wcap};
-        if (wcap > widest.wcap) widest = Geo{nb, apb, box_rows, n_boxes, rows_alloc, 1, wcap};
-        if (best.R >= RUBIX_DEP_MIN_R) break;
+        for (int r = RUBIX_DEP_RMAX; r >= 1; --r)
+            if (31 * r + 1 + 2 * shift + 2 <= slab_w) { R = r; break; }
+        if (R == 0) continue;
+        if (!fast_A) R = std::min(R, 2);
+        const int n_tiles = (tel->n_lambda + 31 * R - 1) / (31 * R);
+        const double cost = n_tiles * (40.0 + 15.0 * R + 6.0 * bands);
+        if (cost < best.cost) best = Geo{apb, bands, ncb, box_w, n_boxes, slab_w, R, cost};
     }
     if (best.R == 0) {
-        // not even 31 bins fit with the full halo: widest slab, 31-bin tiles,
-        // smaller halo; if a tile does not fit at all, global-memory path only
-        best = widest;
-        if (std::max(32.0, 30.0 * A0 + 2.0) + (align - 1) > (double)best.wcap) best.wcap = 0;
+        // no slab fits (very wide Doppler halo): global-memory path only
+        best = Geo{ca, 1, 1, 0, 0, 0, 1, 0.0};
     }
-    h->n_bands = best.bands;
     h->apb = best.apb;
+    h->n_bands = best.bands;
+    h->ncb = best.ncb;
+    h->box_w = best.box_w;
     h->n_boxes = best.n_boxes;
-    h->box_rows = best.box_rows;
-    h->n_rows_alloc = best.rows_alloc;
-    for (int b = 0; b < kMaxBands; ++b) h->band_row0[b] = std::min(b * best.apb, std::max(S.n_age - 1, 0)) * S.n_Z;
+    h->slab_w = best.slab_w;
+    for (int b = 0; b < kMaxBands; ++b) h->band_cell0[b] = std::min(b * best.apb, ca - 1) * h->cz;
     h->tile_w = 31 * best.R;
     h->n_tiles = (tel->n_lambda + h->tile_w - 1) / h->tile_w;
-    h->slab_w = (int)best.wcap;
     std::vector<int> klo(h->n_tiles, 0);
     for (int t = 0; t < h->n_tiles; ++t) {
+        // nodes the tile's fast path reads: K0 .. K0 + 31 R with K0 within
+        // +-shift of the zero-velocity position t00 of its first bin
         const int j0 = t * h->tile_w;
         const double t00 = ((tel->lambda0 + j0 * tel->dlambda) / (1.0 + tel->z_cosmo) - S.ls0) / S.dls;
-        const double span0 = std::max(31.0 * best.R + 1.0, (h->tile_w - 1) * A0 + 2.0);
-        long long k = (long long)std::floor(t00 + 0.5 * span0 - 0.5 * h->slab_w);
-        long long ka = k >= 0 ? (k / align) * align : -(((-k) + align - 1) / align) * align;
-        ka = std::max(-(1ll << 20), std::min(ka, 1ll << 20));
-        klo[t] = (int)ka;
+        const double need = 2.0 * shift + h->tile_w + 3.0;
+        const double k = std::floor(t00 - shift - 1.0 - 0.5 * (h->slab_w - need));
+        klo[t] = (int)std::max(-1e6, std::min(k, 1e6));
     }
     if (dalloc_sync(&h->d_tile_klo, h->n_tiles)) return bail(fail(RUBIX_ERR_OOM, "tile alloc"));
     cudaMemcpy(h->d_tile_klo, klo.data(), klo.size() * 4, cudaMemcpyHostToDevice);
-    h->dep_smem = deposit_smem_bytes(h->n_rows_alloc, std::max(h->slab_w, 0), h->elem);
+    static_assert(kDepHeader % 128 == 0, "slab must start 128-byte aligned");
+    if ((h->box_w * h->ncb * (int)sizeof(float4)) % 128 != 0)
+        return bail(fail(RUBIX_ERR_CUDA, "internal: TMA box of %d x %d quads is not 128-byte aligned", h->box_w, h->ncb));
+    h->dep_smem = deposit_smem_bytes(h->ncb, h->slab_w);
     h->dep_ctas = h->n_sm;
     if (h->slab_w > 0) {
         PFN_encodeTiled_t enc = get_encode_tiled();
         if (!enc) return bail(fail(RUBIX_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"));
-        const CUtensorMapDataType dt = (S.dtype == RUBIX_F32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                     : (S.dtype == RUBIX_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-        cuuint64_t gdim[2] = {(cuuint64_t)S.n_ls, (cuuint64_t)S.n_t};
-        cuuint64_t gstr[1] = {(cuuint64_t)S.pitch * h->elem};
-        cuuint32_t box[2] = {(cuuint32_t)h->slab_w, (cuuint32_t)h->box_rows};
+        // 2-D view of the quads: x = 4 floats per cell (innermost), y = node
+        cuuint64_t gdim[2] = {(cuuint64_t)4 * h->n_cells, (cuuint64_t)S.n_ls};
+        cuuint64_t gstr[1] = {(cuuint64_t)h->n_cells * sizeof(float4)};
+        cuuint32_t box[2] = {(cuuint32_t)(4 * h->ncb), (cuuint32_t)h->box_w};
         cuuint32_t es[2] = {1, 1};
-        CUresult r = enc(&h->tmap, dt, 2, h->d_tpl, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r = enc(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->d_quad, gdim, gstr, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return bail(fail(RUBIX_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r));
     }
     if (cudaDeviceSynchronize() != cudaSuccess)
@@ -602,18 +636,21 @@ DepJob plan_job(const Plan& P, float* target) {
 int enqueue_deposit(const SspState& S, const DepJob* jobs, int n_jobs, long long* d_job_cost, cudaStream_t st) {
     if (n_jobs < 1 || n_jobs > kMaxJobs) return -1;
     DepositParams DP{};
-    DP.ssp = S.ssp;
+    DP.quad = S.d_quad;
+    DP.n_cells = S.n_cells;
+    DP.n_ls = S.ssp.n_ls;
     for (int j = 0; j < n_jobs; ++j) DP.jobs[j] = jobs[j];
     DP.n_jobs = n_jobs;
     DP.job_cost = d_job_cost;
     DP.n_bands = S.n_bands;
-    for (int b = 0; b < kMaxBands; ++b) DP.band_row0[b] = S.band_row0[b];
+    for (int b = 0; b < kMaxBands; ++b) DP.band_cell0[b] = S.band_cell0[b];
     DP.n_lambda = S.n_lambda;
     DP.tile_w = S.tile_w;
     DP.n_tiles = S.n_tiles;
     DP.tile_klo = S.d_tile_klo;
     DP.slab_w = S.slab_w;
-    DP.box_rows = S.box_rows;
+    DP.ncb = S.ncb;
+    DP.box_w = S.box_w;
     DP.n_boxes = S.n_boxes;
     DP.cost_c0 = S.cost_c0;
     DP.err = S.d_err;

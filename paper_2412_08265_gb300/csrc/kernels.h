@@ -12,7 +12,7 @@ struct DepRec;
 struct PartRec;
 struct Item;
 
-constexpr int kMaxBands = 8;
+constexpr int kMaxBands = 32;
 
 // Deposit launch shape: threads per CTA (one CTA per SM: the SSP slab fills
 // shared memory) and how many particle records a warp loads ahead.
@@ -23,16 +23,26 @@ constexpr int kMaxBands = 8;
 #define RUBIX_DEP_PREFETCH 1
 #endif
 // Deposit geometry: particles per work item, the line-of-sight speed (km/s)
-// the shared-memory slab's Doppler halo covers, and the fewest 31-bin rounds
-// per wavelength tile worth adding age bands for.
+// the shared-memory slab's Doppler halo covers, the most 31-bin rounds per
+// wavelength tile, and a fixed number of age bands (0 = chosen by the cost
+// estimate).
 #ifndef RUBIX_DEP_CHUNK
 #define RUBIX_DEP_CHUNK 1024
 #endif
 #ifndef RUBIX_DEP_VHALO
 #define RUBIX_DEP_VHALO 800.0
 #endif
-#ifndef RUBIX_DEP_MIN_R
-#define RUBIX_DEP_MIN_R 5
+#ifndef RUBIX_DEP_RMAX
+#define RUBIX_DEP_RMAX 12
+#endif
+#ifndef RUBIX_DEP_BANDS
+#define RUBIX_DEP_BANDS 0
+#endif
+// How later age bands add to a row the first band wrote: 0 = load, add,
+// store (the row prefetched to L2 when the item starts); 1 = in-order
+// reductions at L2.
+#ifndef RUBIX_DEP_BANDADD
+#define RUBIX_DEP_BANDADD 1
 #endif
 
 // K1 parameters. The sort key is spaxel * n_bands + age band (n_bands <= 1:
@@ -117,25 +127,27 @@ struct DepJob {
     int pad;
 };
 struct DepositParams {
-    SspDev ssp;
+    const float4* quad;      // [n_ls][n_cells] SSP cell quads (the four bilinear corners per node)
+    int n_cells, n_ls;
     DepJob jobs[kMaxJobs];
     int n_jobs;
     long long* job_cost;     // [n_jobs + 1] device scratch: exclusive prefix of the jobs' per-tile cost
     int n_bands;
-    int band_row0[kMaxBands];  // first template row of each band's slab
+    int band_cell0[kMaxBands];  // first cell of each age band's slab
     int n_lambda;
-    int tile_w;              // output bins per tile = 31 * rounds (1..6)
+    int tile_w;              // output bins per tile = 31 * rounds (1..12)
     int n_tiles;
     const int* tile_klo;     // [n_tiles] first SSP node of each tile's slab
-    int slab_w;              // nodes per slab row (0 = no slab: global path only)
-    int box_rows, n_boxes;   // TMA boxes covering one band's template rows
+    int slab_w;              // nodes per slab (0 = no slab: global path only)
+    int ncb;                 // cells per slab node (odd)
+    int box_w, n_boxes;      // TMA boxes of box_w nodes covering the slab
     int cost_c0;             // per-item cost in particle units
     unsigned* err;
     unsigned long long* slow_count;
 };
 int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,
                    cudaStream_t st);
-size_t deposit_smem_bytes(int n_rows_alloc, int slab_w, int elem_bytes);
+size_t deposit_smem_bytes(int ncb, int slab_w);
 
 // K5: combine partial rows of split spaxels in FP64, fixed order.
 int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube,

@@ -1,6 +1,6 @@
-// psf_lsf.cu -- observational effects (Sec. 3: "we apply a point-spread
-// function (PSF) and line-spread function (LSF) convolution and add realistic
-// noise"; Sec. 4: both Gaussian).
+// psf_lsf.cu -- observational effects (Sec. 3: the cube is convolved with the
+// instrument's point-spread and line-spread functions and noise is added;
+// Sec. 4: both functions are Gaussian).
 //
 // The 3-D kernel is separable, g(dy) g(dx) h(dj), with zero padding on every
 // axis. For the radii of the instruments used here a single fused pass

@@ -1,7 +1,7 @@
-// sort.cu -- orientation + spaxel keys (Sec. 3: "orientate the galaxy",
-// "particles are assigned to the IFU spaxels") and the deterministic stable
-// sort of particles by spaxel that replaces global atomics in the per-spaxel
-// sum ("the stellar spectra in each spaxel are summed up").
+// sort.cu -- orientation + spaxel keys (Sec. 3: the galaxy is rotated into the
+// field of view and each particle is assigned to an IFU spaxel) and the
+// deterministic stable sort of particles by spaxel that replaces global
+// atomics in the per-spaxel sum of spectra.
 #include "common.cuh"
 #include "kernels.h"
 
