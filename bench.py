@@ -33,9 +33,10 @@ METRIC = "particle-wavelength deposits/s and p50/p99 cube latency at stated rel 
 UNIT = "deposits/s"
 FLOPS_PER_DEPOSIT = 16  # 4 SSP corners x 2 wavelength neighbours, one FMA each
 REL_ERR_BOUND = 1e-5
-# DRAM bytes (read + write) per deposit launch on the mid-size workload, from the
-# ncu capture summarised in profiles/; None until captured for the current kernel.
-DEPOSIT_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per deposit launch on the mid-size workload (1e6
+# particles), from the ncu capture summarised in profiles/k_deposit_mid-disk-1e6p.md;
+# None when the kernel or the workload differs from that capture.
+DEPOSIT_TRAFFIC_BYTES = 2.477155e9 + 2.718067e9
 
 
 def dist_env():
@@ -393,7 +394,7 @@ def run_ours(args):
     peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
     dep_avg_s = float(np.mean(dep_ms)) / 1e3
     achieved = deposits * FLOPS_PER_DEPOSIT / dep_avg_s / 1e12
-    traffic = DEPOSIT_TRAFFIC_BYTES
+    traffic = DEPOSIT_TRAFFIC_BYTES if args.particles == 1_000_000 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": traffic,
             "kernel": "k_deposit", "kernel_ms": 1e3 * dep_avg_s,

@@ -284,6 +284,53 @@ __device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g
     for (int i = 0; i < R; ++i) acc[i] += bin_value(w4, g4, C, C.j0 + 31 * i + lane, lane, use_slab, slab, quad);
 }
 
+// Fast-path test and per-particle state of the interleaved pair path.
+struct FastState {
+    const float4* q;  // slab quad of node K0 + lane
+    float f, nld, d31;
+};
+template <int R>
+__device__ __forceinline__ bool fast_setup(const float4 g4, const TileCtx& C, const float4* __restrict__ slab,
+                                           int lane, float lanef, FastState& S) {
+    const int c0_bi = __float_as_int(g4.x);
+    const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
+    const int K0 = node_pos(C.j0, bi, g4.y, g4.z, g4.w, S.f);
+    const float delta = (1.f - g4.z) - g4.w;
+    const int kw = K0 - C.klo;
+    const int cr = cell - C.cell0;
+    S.q = slab + (kw + lane) * C.ncb + cr;
+    S.nld = -lanef * delta;
+    S.d31 = 31.f * delta;
+    return delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R) &&
+           (unsigned)cr < (unsigned)C.ncb;
+}
+
+// Two particles of one item at once (both on the fast path): two independent
+// dependency chains per round, one accumulator update for both.
+template <int R>
+__device__ __forceinline__ void deposit_pair(const float4 wa, FastState A, const float4 wb, FastState B,
+                                             const TileCtx& C, int lane, float (&acc)[R]) {
+    const int s31 = 31 * C.ncb, s30 = 30 * C.ncb;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float Ma = quad_dot(wa, *A.q);
+        const float Mb = quad_dot(wb, *B.q);
+        const float ga = A.f + A.nld, gb = B.f + B.nld;
+        const float Xa = __shfl_sync(0xffffffffu, Ma, ga < 0.f ? lane - 1 : lane + 1);
+        const float Xb = __shfl_sync(0xffffffffu, Mb, gb < 0.f ? lane - 1 : lane + 1);
+        const float va = fmaf(fabsf(ga), Xa - Ma, Ma);
+        const float vb = fmaf(fabsf(gb), Xb - Mb, Mb);
+        acc[r] += va + vb;
+        A.f -= A.d31;
+        B.f -= B.d31;
+        const bool ca = A.f < 0.f, cb = B.f < 0.f;
+        A.f = ca ? A.f + 1.f : A.f;
+        B.f = cb ? B.f + 1.f : B.f;
+        A.q += ca ? s30 : s31;
+        B.q += cb ? s30 : s31;
+    }
+}
+
 // Per-tile cost of each job (in-field particles + cost_c0 per work item) and
 // its exclusive prefix, read from the device-side counts of every job.
 __global__ void k_job_cost(const DepositParams P, long long* job_cost) {
@@ -313,6 +360,15 @@ constexpr int kJobChunk = 32;  // jobs per shared-memory work table
 // Work items a warp claims at once (its first lanes look them up together).
 #ifndef RUBIX_DEP_GRAB
 #define RUBIX_DEP_GRAB 4
+#endif
+// Particle records: 1 = the next one loaded into registers ahead, 2 = the next
+// one prefetched into L1.
+#ifndef RUBIX_DEP_RECPF
+#define RUBIX_DEP_RECPF 2
+#endif
+// 1: consecutive particles of an item are deposited two at a time.
+#ifndef RUBIX_DEP_PAIRP
+#define RUBIX_DEP_PAIRP 0
 #endif
 
 template <int R>
@@ -458,6 +514,37 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_c
                     float acc[R];
 #pragma unroll
                     for (int r = 0; r < R; ++r) acc[r] = 0.f;
+#if RUBIX_DEP_PAIRP
+                    int q = q0;
+                    for (; q + 1 < q1; q += 2) {
+                        if (q + 2 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * (q + 2)));
+                        if (q + 3 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * (q + 3)));
+                        const float4 wa = rec4[2 * q], ga4 = rec4[2 * q + 1];
+                        const float4 wb = rec4[2 * q + 2], gb4 = rec4[2 * q + 3];
+                        FastState A, B;
+                        const bool fa = fast_setup<R>(ga4, C, slab, lane, lanef, A);
+                        const bool fb = fast_setup<R>(gb4, C, slab, lane, lanef, B);
+                        if (fa && fb) {
+                            deposit_pair<R>(wa, A, wb, B, C, lane, acc);
+                        } else {
+                            deposit_particle<R>(wa, ga4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
+                            deposit_particle<R>(wb, gb4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
+                        }
+                    }
+                    if (q < q1) {
+                        const float4 w4 = rec4[2 * q], g4 = rec4[2 * q + 1];
+                        deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
+                    }
+#elif RUBIX_DEP_RECPF == 2
+                    // the next particle's record is pulled into L1 while the current
+                    // one is deposited (no registers held across the particle)
+                    if (q0 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * q0));
+                    for (int q = q0; q < q1; ++q) {
+                        if (q + 1 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * (q + 1)));
+                        const float4 w4 = rec4[2 * q], g4 = rec4[2 * q + 1];
+                        deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
+                    }
+#else
                     // the next particle's record is in flight while the current one is deposited
                     float4 wn, gn;
                     if (q0 < q1) {
@@ -472,6 +559,7 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_c
                         }
                         deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
                     }
+#endif
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const int j = C.j0 + 31 * r + lane;

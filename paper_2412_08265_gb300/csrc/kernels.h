@@ -15,12 +15,9 @@ struct Item;
 constexpr int kMaxBands = 32;
 
 // Deposit launch shape: threads per CTA (one CTA per SM: the SSP slab fills
-// shared memory) and how many particle records a warp loads ahead.
+// shared memory; 896 threads leave 72 registers per thread).
 #ifndef RUBIX_DEP_THREADS
-#define RUBIX_DEP_THREADS 1024
-#endif
-#ifndef RUBIX_DEP_PREFETCH
-#define RUBIX_DEP_PREFETCH 1
+#define RUBIX_DEP_THREADS 896
 #endif
 // Deposit geometry: particles per work item, the line-of-sight speed (km/s)
 // the shared-memory slab's Doppler halo covers, the most 31-bin rounds per
