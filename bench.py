@@ -302,6 +302,79 @@ def run_serving(args, dev, ssp):
 
 
 # ---------------------------------------------------------------------------
+# the other single-GPU workloads: the differentiable step (1e6 particles, loss
+# 1/2 |cube - target|^2 against a cube of perturbed ages, metallicities and
+# velocities) and the large galaxy (2e7 particles, BF16 templates)
+# ---------------------------------------------------------------------------
+def _events_ms(torch, fn, stream, steps, flush):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in ev])
+
+
+def run_extra(args, dev, flush):
+    import torch
+    from paper_2412_08265_gb300 import synth
+    from paper_2412_08265_gb300.model import CubeModel
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    # differentiable step
+    wl = synth.mid_galaxy(n=args.particles, seed=1)
+    tgt_p = synth.perturbed_target(wl.particles)
+    model = CubeModel(wl.ssp, wl.telescope, "f32", max_particles=wl.particles.n, device=dev)
+    target = model.forward(tgt_p).clone()
+    d = model.device_particles(wl.particles)
+    cube = torch.empty(model.cube_shape, dtype=torch.float32, device=dev)
+    res = {}
+
+    def step():
+        model.forward(d, out=cube)
+        g = cube - target                      # dL/dcube of 1/2 |cube - target|^2
+        res["grads"] = model.backward(g, want_global=True)
+
+    for _ in range(3):
+        step()
+    n_dep = model.stats()["deposits"]
+    t_step = _events_ms(torch, step, stream, max(3, min(args.steps, 10)), flush)
+    t_fwd = _events_ms(torch, lambda: model.forward(d, out=cube), stream, max(3, min(args.steps, 10)), flush)
+    grads = res["grads"]
+    ok = all(bool(torch.isfinite(x).all()) for x in grads[:4]) and bool(torch.isfinite(grads[4]).all())
+    out["differentiable"] = {
+        "workload": "mid-disk-1e6p-150x150x3721-f32, loss 1/2|cube - target|^2, target: ages/Z x (1 + N(0, 0.1)), v + 20 km/s",
+        "step_ms": float(np.median(t_step)), "forward_ms": float(np.median(t_fwd)),
+        "backward_ms": float(np.median(t_step) - np.median(t_fwd)),
+        "deposits_per_s_forward_plus_backward": 2.0 * n_dep / (float(np.median(t_step)) / 1e3),
+        "grads_finite": ok}
+    model.close()
+    del d, cube, target
+    # large galaxy, BF16 templates
+    wl = synth.large_galaxy()
+    model = CubeModel(wl.ssp, wl.telescope, "bf16", max_particles=wl.particles.n, device=dev)
+    d = model.device_particles(wl.particles)
+    cube = torch.empty(model.cube_shape, dtype=torch.float32, device=dev)
+    for _ in range(2):
+        model.forward(d, out=cube)
+    st = model.stats()
+    model.set_profiling(True)
+    t = _events_ms(torch, lambda: model.forward(d, out=cube), stream, 3, flush)
+    dep = model.profile_history("deposit")
+    psf = model.profile_history("psf_lsf")
+    model.set_profiling(False)
+    out["large_bf16"] = {
+        "workload": wl.name, "n_in_fov": st["n_in_fov"], "ms_per_step": float(np.median(t)),
+        "deposits_per_s": st["deposits"] / (float(np.median(t)) / 1e3),
+        "deposit_ms": float(np.median(dep)), "psf_lsf_ms": float(np.median(psf)),
+        "tile_bins": st["tile_w"], "age_bands": st["n_bands"]}
+    model.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -426,6 +499,8 @@ def run_ours(args):
             "clocks": clk, "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "stage_ms_last_step": stage_last}
+    if not args.no_extra:
+        line["workloads"] = run_extra(args, dev, flush)
     if args.serve_requests > 0:
         line["serving"] = run_serving(args, dev, wl.ssp)
     print(json.dumps(line), flush=True)
@@ -445,6 +520,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--particles", type=int, default=1_000_000,
                     help="particles of the mid-size galaxy (smaller only for profiler captures)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the differentiable-step and large-galaxy measurements")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="requests in the serving stream (0 = no serving run)")
     ap.add_argument("--serve-load", type=float, default=0.9,

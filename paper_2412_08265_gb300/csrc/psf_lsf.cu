@@ -109,7 +109,13 @@ __global__ void __launch_bounds__(256) k_psfy_noise(const ConvParams P, const fl
 #ifndef RUBIX_PSF_STAGES
 #define RUBIX_PSF_STAGES 3      // input rows in flight (cp.async pipeline depth)
 #endif
-constexpr int kFX = 48, kFL = 32, kFY = 50;  // kFL must equal the warp width
+#ifndef RUBIX_PSF_FX
+#define RUBIX_PSF_FX 32         // spaxels along x per CTA (a multiple of 8)
+#endif
+#ifndef RUBIX_PSF_FY
+#define RUBIX_PSF_FY 50         // output rows along y per CTA
+#endif
+constexpr int kFX = RUBIX_PSF_FX, kFL = 32, kFY = RUBIX_PSF_FY;  // kFL must equal the warp width
 constexpr int kFThreads = 256;
 constexpr int kFWarps = kFThreads / 32;
 constexpr int kFXW = kFX / kFWarps;          // output x rows owned by each warp

@@ -207,6 +207,42 @@ def test_forward_mid_galaxy_sampled_spaxels(torch_cuda):
     model.close()
 
 
+def test_forward_large_bf16_sampled_spaxels(torch_cuda):
+    """Large workload (2e7 particles, 30 % bulge, 300x300 spaxels x 3721 bins,
+    BF16 templates) in the bench's launch configuration. Sampled spaxels
+    against the FP64 oracle: within the BF16 bound on the original templates,
+    within the FP32 bound on the BF16-rounded templates (same arithmetic);
+    total flux of the sampled spaxels within the BF16 bound."""
+    wl = synth.large_galaxy()
+    tel = wl.telescope
+    model = make_model(wl, dtype="bf16", n=wl.particles.n)
+    got = model.forward(wl.particles).cpu().numpy()
+    xp, yp, v = oracle.orient(wl.particles)
+    key = oracle.spaxel_keys(xp, yp, tel)
+    counts = np.bincount(key, minlength=tel.nx * tel.ny + 1)[:-1]
+    rng = np.random.default_rng(23)
+    heavy = np.argsort(counts)[-2:]
+    rand = rng.choice(np.flatnonzero(counts > 0), 4, replace=False)
+    edge = np.array([0, tel.nx * tel.ny - 1])
+    sel = np.unique(np.concatenate([heavy, rand, edge])).astype(np.int32)
+    mask = np.zeros(tel.nx * tel.ny, np.uint8)
+    r = 3
+    for s_ in sel:
+        y, x = divmod(int(s_), tel.nx)
+        for yy in range(max(0, y - r), min(tel.ny, y + r + 1)):
+            mask[yy * tel.nx + max(0, x - r): yy * tel.nx + min(tel.nx, x + r + 1)] = 1
+    g = got.reshape(-1, tel.n_lambda)[sel].astype(np.float64)
+    for spectra, tol in ((None, TOL_BF16), (bf16_round(wl.ssp.spectra), TOL_F32)):
+        cube0 = oracle.deposit(key, v, wl.particles, wl.ssp, tel, mask=mask, n_threads=NT, spectra=spectra)
+        ref = oracle.psf_lsf_at(cube0, tel, sel)
+        del cube0
+        assert float(np.abs(g - ref).max()) / float(np.abs(ref).max()) <= tol
+        assert abs(g.sum() / ref.sum() - 1.0) <= TOL_BF16
+    st = model.stats()
+    assert st["device_error"] == 0 and st["n_in_fov"] == int(counts.sum())
+    model.close()
+
+
 def test_deterministic_bitwise(torch_cuda):
     wl = synth.mid_galaxy(n=200_000)
     model = make_model(wl, n=wl.particles.n)
