@@ -1,0 +1,350 @@
+// adjoint_tiles.cu -- the adjoint of the deposit (gradients through the
+// pipeline, Abstract and Sec. 1) over the deposit's own decomposition.
+//
+// For particle p with unit-mass bilinear weights W_c(ta, tz), the spectrum at
+// bin j is S_j = sum_c W_c lerp(T_c, t_j) and the loss sees it through
+// G_j = dL/dcube0[s_p, j]. The gradient needs, per particle,
+//   sm  = sum_j G_j S_j                      (dL/dm = flux_scale * sm)
+//   sla = sum_j G_j dS_j/dta                 (chain rule to age outside)
+//   slz = sum_j G_j dS_j/dtz                 (to Z outside)
+//   sv  = sum_j G_j dS_j/dt * (t_j + ls0/dls) (times dt/dv / t_abs outside)
+// dS/dta and dS/dtz are bilinear forms in the same four corners with weights
+// a = (-(1-tz), 1-tz, -tz, tz) and b = (-(1-ta), -ta, 1-ta, ta), so each is
+// one more dot product with the quad of the node. The deposit's (tile, work
+// item, age band) partition, quad slabs and 31-bin rounds carry over
+// unchanged: lane l forms M, A, B at node K0 + o_r + l, the neighbour node's
+// three values arrive by shuffle, and the lane accumulates G_j times the
+// interpolated values over its bins. A warp reduction per (particle, tile)
+// gives part[tile][particle]; K8 adds the tiles in FP64 in tile order.
+#include "common.cuh"
+#include "kernels.h"
+#include "tile.cuh"
+
+namespace rubix {
+
+// ---------------------------------------------------------------------------
+// Setup: unit-mass weights per sorted particle (zero when the spectrum misses
+// every output bin, as in the forward).
+// ---------------------------------------------------------------------------
+__global__ void k_adj_setup(const AdjointParams P, const DepRec* __restrict__ rec, float4* __restrict__ wu) {
+    const long long n_in = P.seg_off[(long long)P.n_s * P.n_bands];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_in;
+         i += (long long)gridDim.x * blockDim.x) {
+        const PartRec pr = P.prec[i];
+        int ia, iz;
+        float ta, tz, dta, dtz;
+        ssp_cell(log10f(pr.age), P.ssp.la_nodes, P.ssp.n_age, ia, ta, dta);
+        ssp_cell(log10f(pr.Z), P.ssp.lz_nodes, P.ssp.n_Z, iz, tz, dtz);
+        const bool live = rec[i].a_hi > 0.f;
+        wu[i] = live ? make_float4((1.f - ta) * (1.f - tz), ta * (1.f - tz), (1.f - ta) * tz, ta * tz)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+int launch_adjoint_setup(const AdjointParams& P, const DepRec* rec, float4* wu, cudaStream_t st) {
+    if (P.n_in <= 0) return 0;
+    long long nb = (P.n_in + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    k_adj_setup<<<(int)nb, 256, 0, st>>>(P, rec, wu);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// Per (particle, tile) sums.
+// ---------------------------------------------------------------------------
+struct AdjSums {
+    float sm, sa, sz, sv;
+};
+
+// General path: bins of this tile one at a time, quads from the slab when
+// every bin of the warp has its node pair there, else from global memory.
+template <int R>
+__device__ __noinline__ AdjSums adj_general(const float4 w, const float4 g4, const TileCtx C, const float4* slab,
+                                            const float4* quad, int lane, const float (&G)[R], float ls0_over) {
+    const int c0_bi = __float_as_int(g4.x);
+    const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
+    bool ok = C.slab_w > 0 && (unsigned)(cell - C.cell0) < (unsigned)C.ncb;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = C.j0 + 31 * r + lane;
+        if (lane < 31 && j < C.n_lambda) {
+            float f;
+            const int k = node_pos(j, bi, g4.y, g4.z, g4.w, f) - C.klo;
+            ok = ok && k >= 0 && k + 1 < C.slab_w;
+        }
+    }
+    const bool use_slab = __all_sync(0xffffffffu, ok);
+    const float s01 = w.x + w.y, s23 = w.z + w.w, s02 = w.x + w.z, s13 = w.y + w.w;
+    AdjSums S{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = C.j0 + 31 * r + lane;
+        if (lane == 31 || j >= C.n_lambda) continue;
+        float f;
+        const int k = node_pos(j, bi, g4.y, g4.z, g4.w, f);
+        float4 q0, q1;
+        if (use_slab) {
+            const float4* p = slab + (k - C.klo) * C.ncb + (cell - C.cell0);
+            q0 = p[0];
+            q1 = p[C.ncb];
+        } else {
+            q0 = quad_global(quad, C.n_cells, C.n_ls, cell, k);
+            q1 = quad_global(quad, C.n_cells, C.n_ls, cell, k + 1);
+        }
+        const float m0 = quad_dot(w, q0), m1 = quad_dot(w, q1);
+        const float a0 = s01 * (q0.y - q0.x) + s23 * (q0.w - q0.z), a1 = s01 * (q1.y - q1.x) + s23 * (q1.w - q1.z);
+        const float b0 = s02 * (q0.z - q0.x) + s13 * (q0.w - q0.y), b1 = s02 * (q1.z - q1.x) + s13 * (q1.w - q1.y);
+        const float Gj = G[r];
+        S.sm = fmaf(Gj, fmaf(f, m1 - m0, m0), S.sm);
+        S.sa = fmaf(Gj, fmaf(f, a1 - a0, a0), S.sa);
+        S.sz = fmaf(Gj, fmaf(f, b1 - b0, b0), S.sz);
+        S.sv = fmaf(Gj * (m1 - m0), ((float)k + f) + ls0_over, S.sv);
+    }
+    return S;
+}
+
+template <int R>
+__device__ __forceinline__ AdjSums adj_particle(const float4 w, const float4 g4, const TileCtx& C,
+                                                const float4* __restrict__ slab, const float4* __restrict__ quad,
+                                                int lane, float lanef, const float (&G)[R], float ls0_over) {
+    const int c0_bi = __float_as_int(g4.x);
+    const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
+    float f;
+    const int K0 = node_pos(C.j0, bi, g4.y, g4.z, g4.w, f);
+    const float delta = (1.f - g4.z) - g4.w;
+    const int kw = K0 - C.klo;
+    const int cr = cell - C.cell0;
+    if (!(delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R) &&
+          (unsigned)cr < (unsigned)C.ncb))
+        return adj_general<R>(w, g4, C, slab, quad, lane, G, ls0_over);
+    const float s01 = w.x + w.y, s23 = w.z + w.w, s02 = w.x + w.z, s13 = w.y + w.w;
+    const float4* q = slab + (kw + lane) * C.ncb + cr;
+    const int s31 = 31 * C.ncb, s30 = 30 * C.ncb;
+    const float nld = -lanef * delta;
+    const float d31 = 31.f * delta;
+    float tb = ((float)K0 + lanef) + ls0_over;  // absolute node position of lane l's node, / dls
+    AdjSums S{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float4 Q = *q;
+        const float M = quad_dot(w, Q);
+        const float A = s01 * (Q.y - Q.x) + s23 * (Q.w - Q.z);
+        const float B = s02 * (Q.z - Q.x) + s13 * (Q.w - Q.y);
+        const float g = f + nld;
+        const bool neg = g < 0.f;
+        const int src = neg ? lane - 1 : lane + 1;
+        const float XM = __shfl_sync(0xffffffffu, M, src);
+        const float XA = __shfl_sync(0xffffffffu, A, src);
+        const float XB = __shfl_sync(0xffffffffu, B, src);
+        const float ag = fabsf(g);
+        const float Gj = G[r];  // 0 for lane 31 and bins past the end
+        const float dM = XM - M;
+        S.sm = fmaf(Gj, fmaf(ag, dM, M), S.sm);
+        S.sa = fmaf(Gj, fmaf(ag, XA - A, A), S.sa);
+        S.sz = fmaf(Gj, fmaf(ag, XB - B, B), S.sz);
+        // slope between the bracketing nodes, times the bin's node position
+        S.sv = fmaf(Gj * (neg ? -dM : dM), tb + g, S.sv);
+        f -= d31;
+        const bool carry = f < 0.f;
+        f = carry ? f + 1.f : f;
+        q += carry ? s30 : s31;
+        tb += carry ? 30.f : 31.f;
+    }
+    return S;
+}
+
+template <int R>
+__global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_adjoint_tiles(const __grid_constant__ AdjTileParams P,
+                                                                         const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    int* s_next = reinterpret_cast<int*>(smem + 16);
+    float4* slab = reinterpret_cast<float4*>(smem + kDepHeader);
+    const int lane = threadIdx.x & 31;
+    const float lanef = (float)lane;
+    const int nb = P.n_bands;
+    const long long n_items = P.item_off[P.n_s];
+    const long long n_in = P.seg_off[(long long)P.n_s * nb];
+    if (n_in > P.n_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(P.err, kErrBadItem);
+        return;
+    }
+    const long long C0 = P.cost_c0;
+    const long long CT = n_in + C0 * n_items;
+    if (CT <= 0) return;
+    const long long total = CT * P.n_tiles;
+    const long long lo = total * blockIdx.x / gridDim.x;
+    const long long hi = total * (blockIdx.x + 1) / gridDim.x;
+    if (lo >= hi) return;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    TileCtx C;
+    C.slab_w = P.slab_w;
+    C.ncb = P.ncb;
+    C.n_lambda = P.n_lambda;
+    C.n_ls = P.n_ls;
+    C.n_cells = P.n_cells;
+    const uint32_t slab_bytes = (uint32_t)P.n_boxes * (uint32_t)P.box_w * (uint32_t)P.ncb * sizeof(float4);
+    uint32_t phase = 0;
+    const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(P.rec);
+
+    for (long long t = lo / CT; t < P.n_tiles && t * CT < hi; ++t) {
+        const long long a = max(lo - t * CT, 0ll), b = min(hi - t * CT, CT);
+        if (a >= b) continue;
+        const int ia = (int)item_lower_bound(P.items, n_items, C0, a);
+        const int ib = (int)item_lower_bound(P.items, n_items, C0, b);
+        const int nv = ib - ia;
+        C.klo = P.tile_klo[t];
+        C.j0 = (int)t * P.tile_w;
+        float4* __restrict__ part = P.part + t * P.n_cap;
+        for (int band = 0; band < nb; ++band) {
+            C.cell0 = P.band_cell0[band];
+            __syncthreads();  // all warps are done with the previous slab
+            if (threadIdx.x == 0) {
+                *s_next = 0;
+                if (C.slab_w > 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(bar, slab_bytes);
+                    for (int bx = 0; bx < P.n_boxes; ++bx)
+                        tma_load_2d(slab + (size_t)bx * P.box_w * C.ncb, &tmap, bar, 4 * C.cell0,
+                                    C.klo + bx * P.box_w);
+                }
+            }
+            bool ok = true;
+            if (C.slab_w > 0) {
+                ok = mbar_wait_bounded(bar, phase, 4000000000ll);
+                phase ^= 1u;
+            }
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(P.err, kErrTmaTimeout);
+                return;
+            }
+            constexpr int GR = RUBIX_DEP_GRAB;
+            while (true) {
+                int v0 = 0;
+                if (lane == 0) v0 = atomicAdd(s_next, GR);
+                v0 = __shfl_sync(0xffffffffu, v0, 0);
+                if (v0 >= nv) break;
+                int qb = 0, qe = 0, sp = 0;
+                bool live = false;
+                if (lane < GR && v0 + lane < nv) {
+                    const Item I = P.items[ia + v0 + lane];
+                    sp = I.spaxel;
+                    if (sp < 0 || sp >= P.n_s) {
+                        atomicOr(P.err, kErrBadItem);
+                    } else {
+                        qb = I.begin;
+                        qe = I.end;
+                        if (nb > 1) {
+                            qb = max(qb, P.seg_off[(long long)sp * nb + band]);
+                            qe = min(qe, P.seg_off[(long long)sp * nb + band + 1]);
+                        }
+                        live = qb < qe;
+                    }
+                }
+                unsigned m = __ballot_sync(0xffffffffu, live);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int q0 = __shfl_sync(0xffffffffu, qb, src);
+                    const int q1 = __shfl_sync(0xffffffffu, qe, src);
+                    const int s = __shfl_sync(0xffffffffu, sp, src);
+                    // this tile's slice of the spaxel's dL/dcube0 row, one bin per lane and round
+                    float G[R];
+                    const float* __restrict__ grow = P.G0 + (long long)s * P.n_lambda;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int j = C.j0 + 31 * r + lane;
+                        G[r] = (lane < 31 && j < P.n_lambda) ? grow[j] : 0.f;
+                    }
+                    for (int q = q0; q < q1; ++q) {
+                        if (q + 1 < q1) {
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(P.wu + q + 1));
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * (q + 1) + 1));
+                        }
+                        AdjSums S = adj_particle<R>(P.wu[q], rec4[2 * q + 1], C, slab, P.quad, lane, lanef, G,
+                                                    P.ls0_over);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            S.sm += __shfl_xor_sync(0xffffffffu, S.sm, o);
+                            S.sa += __shfl_xor_sync(0xffffffffu, S.sa, o);
+                            S.sz += __shfl_xor_sync(0xffffffffu, S.sz, o);
+                            S.sv += __shfl_xor_sync(0xffffffffu, S.sv, o);
+                        }
+                        if (lane == 0) part[q] = make_float4(S.sm, S.sa, S.sz, S.sv);
+                    }
+                }
+            }
+        }
+    }
+}
+
+int launch_adjoint_tiles(const AdjTileParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,
+                         cudaStream_t st) {
+    if (P.tile_w % 31 != 0) return -1;
+    void (*fn)(const AdjTileParams, const CUtensorMap) = nullptr;
+    switch (P.tile_w / 31) {
+#define RUBIX_ADJ_R(r) \
+    case r: fn = k_adjoint_tiles<r>; break;
+        RUBIX_ADJ_R(1) RUBIX_ADJ_R(2) RUBIX_ADJ_R(3) RUBIX_ADJ_R(4) RUBIX_ADJ_R(5) RUBIX_ADJ_R(6)
+        RUBIX_ADJ_R(7) RUBIX_ADJ_R(8) RUBIX_ADJ_R(9) RUBIX_ADJ_R(10) RUBIX_ADJ_R(11) RUBIX_ADJ_R(12)
+#undef RUBIX_ADJ_R
+        default: return -1;
+    }
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    fn<<<n_ctas, threads, smem, st>>>(P, *tmap);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// K8: tiles summed in FP64 (tile order), chain rule, original order.
+// ---------------------------------------------------------------------------
+__global__ void k_adj_final(const AdjointParams P, const float4* __restrict__ part, int n_tiles, long long n_cap) {
+    const long long n_in = P.seg_off[(long long)P.n_s * P.n_bands];
+    const float ln10 = 2.302585092994046f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_in;
+         i += (long long)gridDim.x * blockDim.x) {
+        double sm = 0.0, sa = 0.0, sz = 0.0, sv = 0.0;
+        for (int t = 0; t < n_tiles; ++t) {
+            const float4 v = part[t * n_cap + i];
+            sm += v.x;
+            sa += v.y;
+            sz += v.z;
+            sv += v.w;
+        }
+        const PartRec pr = P.prec[i];
+        int ia, iz;
+        float ta, tz, dta, dtz;
+        ssp_cell(log10f(pr.age), P.ssp.la_nodes, P.ssp.n_age, ia, ta, dta);
+        ssp_cell(log10f(pr.Z), P.ssp.lz_nodes, P.ssp.n_Z, iz, tz, dtz);
+        // dt/dv = -(t + ls0/dls) / (c (1 + v/c)): the sums carry the (t + ls0/dls) factor
+        const float q = (float)(-1.0 / (kC_kms * (1.0 + (double)pr.v / kC_kms)));
+        const float fs = (float)P.flux_scale;
+        const float dm = fs * (float)sm;
+        const float dage = fs * pr.mass * dta * (float)sa / (pr.age * ln10);
+        const float dZ = fs * pr.mass * dtz * (float)sz / (pr.Z * ln10);
+        const float dv = fs * pr.mass * q * (float)sv;
+        const int p = P.perm[i];
+        if (P.d_mass) P.d_mass[p] = dm;
+        if (P.d_age) P.d_age[p] = dage;
+        if (P.d_Z) P.d_Z[p] = dZ;
+        if (P.d_v) P.d_v[p] = dv;
+        if (P.contrib) {
+            P.contrib[2 * i] = (double)dv;
+            P.contrib[2 * i + 1] = (double)pr.mass * (double)dm;
+        }
+    }
+}
+
+int launch_adjoint_final(const AdjointParams& P, const float4* part, int n_tiles, long long n_cap, cudaStream_t st) {
+    if (P.n_in <= 0) return 0;
+    long long nb = (P.n_in + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    k_adj_final<<<(int)nb, 256, 0, st>>>(P, part, n_tiles, n_cap);
+    return 1;
+}
+
+}  // namespace rubix

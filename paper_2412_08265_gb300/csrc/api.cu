@@ -282,7 +282,41 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     A.d_v = d_vlos;
     A.contrib = d_global ? P.d_contrib : nullptr;
     A.n_in = P.last_n;  // upper bound; the kernel reads the in-field count on the device
-    launch_adjoint_rec(A, P.d_rec, st);
+#ifdef RUBIX_ADJ_WARP
+    launch_adjoint_rec(A, P.d_rec, st);  // one warp per particle over every bin
+#else
+    // over the deposit's (tile, work item, age band) decomposition and slabs
+    launch_adjoint_setup(A, P.d_rec, P.d_wu, st);
+    AdjTileParams T{};
+    T.quad = S.d_quad;
+    T.n_cells = S.n_cells;
+    T.n_ls = S.ssp.n_ls;
+    T.rec = P.d_rec;
+    T.wu = P.d_wu;
+    T.items = P.d_items;
+    T.item_off = P.d_item_off;
+    T.seg_off = P.d_seg_off;
+    T.n_s = P.n_s;
+    T.n_bands = S.n_bands;
+    for (int b = 0; b < kMaxBands; ++b) T.band_cell0[b] = S.band_cell0[b];
+    T.G0 = G0;
+    T.part = P.d_adjpart;
+    T.n_cap = P.cap;
+    T.n_lambda = P.tel.n_lambda;
+    T.tile_w = S.tile_w;
+    T.n_tiles = S.n_tiles;
+    T.tile_klo = S.d_tile_klo;
+    T.slab_w = S.slab_w;
+    T.ncb = S.ncb;
+    T.box_w = S.box_w;
+    T.n_boxes = S.n_boxes;
+    T.cost_c0 = S.cost_c0;
+    T.ls0_over = (float)(S.ssp.ls0 / S.ssp.dls);
+    T.err = S.d_err;
+    if (launch_adjoint_tiles(T, &S.tmap, S.dep_ctas, S.dep_threads, S.dep_smem, st) < 0)
+        return fail(RUBIX_ERR_CUDA, "adjoint launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    launch_adjoint_final(A, P.d_adjpart, S.n_tiles, P.cap, st);
+#endif
     if (d_global)
         launch_reduce_global(P.d_contrib, P.d_seg_off + (size_t)P.n_s * S.n_bands, d_global, P.d_red, st);
     CK(cudaGetLastError());

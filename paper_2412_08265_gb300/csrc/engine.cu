@@ -392,6 +392,8 @@ std::vector<Buf> plan_buffers(Plan* P, const SspState& S, int n_s, int n_lambda,
     if (with_grad) {
         v.push_back({(void**)&P->d_contrib, 16 * N});
         v.push_back({(void**)&P->d_red, 8 * 1024});
+        v.push_back({(void**)&P->d_wu, 16 * N});
+        v.push_back({(void**)&P->d_adjpart, 16 * N * (size_t)std::max(S.n_tiles, 1)});
     }
     return v;
 }

@@ -88,6 +88,8 @@ struct Plan {
     float *d_cube0 = nullptr, *d_tmp = nullptr, *d_out = nullptr;
     long long* d_job_cost = nullptr;        // deposit launch scratch [kMaxJobs + 1]
     double *d_contrib = nullptr, *d_red = nullptr;
+    float4* d_wu = nullptr;                 // backward: unit-mass weights [cap]
+    float4* d_adjpart = nullptr;            // backward: per (tile, particle) sums [n_tiles][cap]
     Alloc alloc;
     size_t bytes = 0;                       // device bytes held by the plan
     // state of the last forward

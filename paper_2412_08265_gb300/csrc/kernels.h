@@ -38,6 +38,10 @@ constexpr int kMaxBands = 32;
 // How later age bands add to a row the first band wrote: 0 = load, add,
 // store (the row prefetched to L2 when the item starts); 1 = in-order
 // reductions at L2.
+// Work items a warp claims at once (its first lanes look them up together).
+#ifndef RUBIX_DEP_GRAB
+#define RUBIX_DEP_GRAB 4
+#endif
 #ifndef RUBIX_DEP_BANDADD
 #define RUBIX_DEP_BANDADD 1
 #endif
@@ -179,6 +183,38 @@ struct AdjointParams {
     long long n_in;            // upper bound (grid sizing)
 };
 int launch_adjoint_rec(const AdjointParams& P, const DepRec* rec, cudaStream_t st);
+
+// Adjoint over the deposit's (wavelength tile, work item, age band)
+// decomposition: per (tile, particle) the four sums
+//   part = (sum_j G S, sum_j G dS/dta', sum_j G dS/dtz', sum_j G dS/dt * t_abs)
+// over the tile's bins (unit mass), from the same shared-memory quad slabs.
+struct AdjTileParams {
+    const float4* quad;
+    int n_cells, n_ls;
+    const DepRec* rec;          // [n_in] forward records (sorted order)
+    const float4* wu;           // [n_in] unit-mass bilinear weights (0: spectrum misses every bin)
+    const Item* items;
+    const int* item_off;        // [n_s + 1]
+    const int* seg_off;         // [n_s * n_bands + 2]
+    int n_s, n_bands;
+    int band_cell0[kMaxBands];
+    const float* G0;            // [n_s][n_lambda] dL/d(cube before PSF/LSF)
+    float4* part;               // [n_tiles][n_cap]
+    long long n_cap;
+    int n_lambda, tile_w, n_tiles;
+    const int* tile_klo;
+    int slab_w, ncb, box_w, n_boxes;
+    int cost_c0;
+    float ls0_over;             // ls0 / dls: node index -> rest wavelength / dls
+    unsigned* err;
+};
+int launch_adjoint_tiles(const AdjTileParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,
+                         cudaStream_t st);
+// Unit-mass bilinear weights per sorted particle (K7 setup).
+int launch_adjoint_setup(const AdjointParams& P, const DepRec* rec, float4* wu, cudaStream_t st);
+// Sum of the tiles' parts in FP64 (tile order) and the chain rule to
+// dL/d(mass, age, Z, v_los) in original order (+ contributions to global sums).
+int launch_adjoint_final(const AdjointParams& P, const float4* part, int n_tiles, long long n_cap, cudaStream_t st);
 int launch_zero_grads(float* a, float* b, float* c, float* d, long long n, cudaStream_t st);
 int launch_reduce_global(const double* contrib, const int* n_in_dev, double* out2, double* scratch, cudaStream_t st);
 
