@@ -100,6 +100,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def whole_job(units: float, seconds: float, device=None):
+    """Whole-job aggregate over the ranks of the default process group: the
+    units all ranks processed and the slowest rank's time (a single process
+    returns its own). Returns (units / seconds, units, seconds)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units / seconds, units, seconds
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()) / float(t.item()), float(u.item()), float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -426,12 +441,10 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    total_s = float(step_ms.sum()) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = deposits * args.steps * ws / total_s
+    # every rank forward-models its own galaxy: deposits summed over ranks,
+    # time of the slowest rank
+    value, _, total_s = whole_job(deposits * args.steps, float(step_ms.sum()) / 1e3, device=dev)
+    n_in_all = whole_job(n_in * args.steps, 1.0, device=dev)[1]
     model.set_profiling(False)
 
     # ---- end to end through the C ABI with host buffers ----
@@ -495,7 +508,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}"},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "rel_err_bound": REL_ERR_BOUND, "rel_err_sampled": rel,
-            "particles_per_s": n_in * args.steps * ws / total_s,
+            "particles_per_s": n_in_all / total_s,
             "clocks": clk, "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "stage_ms_last_step": stage_last}

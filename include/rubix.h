@@ -284,6 +284,15 @@ rubix_status rubix_serve_stats(rubix_server_t *srv, int64_t *stats, int32_t *n_i
  * free the server. */
 rubix_status rubix_serve_destroy(rubix_server_t *srv);
 
+/* Self-test of failure detection (no counterpart in the paper). Every wait in
+ * the library's kernels is bounded: when it runs out it sets a bit in the
+ * device error word (reported as RUBIX_ERR_DEVICE) and the kernel returns.
+ * This call launches one 32-thread kernel on the current device that waits on
+ * a shared-memory barrier nothing completes, with that bounded wait and a
+ * limit of limit_s seconds (0 < limit_s <= 10), and waits for it: *timed_out
+ * is 1 when the wait gave up and the kernel returned. The device stays usable. */
+rubix_status rubix_selftest_bounded_wait(double limit_s, int32_t *timed_out);
+
 /* Thread-local message for the last non-OK status returned on this thread. */
 const char *rubix_last_error_message(void);
 

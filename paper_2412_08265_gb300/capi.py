@@ -91,6 +91,7 @@ _SIGS = {
     "rubix_serve_cancel": (C.c_int32, [C.c_void_p, C.c_uint64]),
     "rubix_serve_stats": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "rubix_serve_destroy": (C.c_int32, [C.c_void_p]),
+    "rubix_selftest_bounded_wait": (C.c_int32, [C.c_double, C.POINTER(C.c_int32)]),
     "rubix_last_error_message": (C.c_char_p, []),
     "rubix_version": (C.c_char_p, []),
 }
@@ -247,6 +248,13 @@ def rubix_serve_stats(srv: int) -> list[int]:
 
 def rubix_serve_destroy(srv: int) -> None:
     _call("rubix_serve_destroy", C.c_void_p(srv))
+
+
+def rubix_selftest_bounded_wait(limit_s: float) -> bool:
+    """True when a device wait with nothing to complete it gave up after limit_s."""
+    t = C.c_int32(0)
+    _call("rubix_selftest_bounded_wait", C.c_double(limit_s), C.byref(t))
+    return bool(t.value)
 
 
 def last_error_message() -> str:

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -436,6 +437,14 @@ void plan_release(Plan* P) {
     P->cap = 0;
 }
 
+// Host-side fault injection for tests: RUBIX_FAULT_ALLOC_AT=k makes the k-th
+// buffer allocation of every plan fail as if the device were out of memory
+// (nothing is run on the GPU; the plan's other buffers are released).
+static int fault_alloc_at() {
+    const char* e = std::getenv("RUBIX_FAULT_ALLOC_AT");
+    return e ? std::atoi(e) : 0;
+}
+
 rubix_status plan_init(Plan* P, const SspState* S, const rubix_telescope* tel, long long n, Alloc a, bool with_out,
                        bool with_grad) {
     rubix_status st = validate_telescope(tel, S->ssp.dls);
@@ -467,9 +476,12 @@ rubix_status plan_init(Plan* P, const SspState* S, const rubix_telescope* tel, l
     P->part_cap = 2 * (P->cap / S->chunk) + 2;
     const bool need_tmp = psf_lsf_needs_tmp(C.rp, C.rl);
     P->bytes = 0;
+    const int fail_at = fault_alloc_at();
+    int idx = 0;
     for (const Buf& b : plan_buffers(P, *S, P->n_s, tel->n_lambda, P->cap, with_out, with_grad, need_tmp, a.staging)) {
         cudaError_t e;
-        if (!a.async) e = cudaMalloc(b.ptr, round256(b.bytes));
+        if (++idx == fail_at) e = cudaErrorMemoryAllocation;
+        else if (!a.async) e = cudaMalloc(b.ptr, round256(b.bytes));
         else if (a.pool) e = cudaMallocFromPoolAsync(b.ptr, round256(b.bytes), a.pool, a.stream);
         else e = cudaMallocAsync(b.ptr, round256(b.bytes), a.stream);
         if (e != cudaSuccess) {
