@@ -291,6 +291,10 @@ int launch_adjoint_tiles(const AdjTileParams& P, const CUtensorMap* tmap, int n_
     case r: fn = k_adjoint_tiles<r>; break;
         RUBIX_ADJ_R(1) RUBIX_ADJ_R(2) RUBIX_ADJ_R(3) RUBIX_ADJ_R(4) RUBIX_ADJ_R(5) RUBIX_ADJ_R(6)
         RUBIX_ADJ_R(7) RUBIX_ADJ_R(8) RUBIX_ADJ_R(9) RUBIX_ADJ_R(10) RUBIX_ADJ_R(11) RUBIX_ADJ_R(12)
+#if RUBIX_DEP_RMAX > 12
+        RUBIX_ADJ_R(13) RUBIX_ADJ_R(14) RUBIX_ADJ_R(15) RUBIX_ADJ_R(16) RUBIX_ADJ_R(17) RUBIX_ADJ_R(18)
+        RUBIX_ADJ_R(19) RUBIX_ADJ_R(20) RUBIX_ADJ_R(21) RUBIX_ADJ_R(22) RUBIX_ADJ_R(23) RUBIX_ADJ_R(24)
+#endif
 #undef RUBIX_ADJ_R
         default: return -1;
     }

@@ -258,7 +258,8 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
         // the PSF and LSF kernels are symmetric: their adjoint is the same convolution
         ConvParams C = P.conv;
         C.noise_inv_s2n = 0.f;
-        launch_psf_lsf(C, dL_dcube, P.d_tmp, P.d_cube0, st);
+        if (launch_psf_lsf(C, dL_dcube, P.tel.n_lambda, nullptr, P.d_tmp, P.d_cube0, st) < 0)
+            return fail(RUBIX_ERR_CUDA, "PSF/LSF transpose launch failed");
         G0 = P.d_cube0;
     }
     launch_zero_grads(d_mass, d_age, d_Z, d_vlos, P.last_n, st);

@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_c
                     const int pr = __shfl_sync(0xffffffffu, prow, src);
                     const DepJob& J = P.jobs[s_job[k]];
                     const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(J.rec);
-                    float* dst = (pr < 0) ? J.cube + (long long)s * P.n_lambda
+                    float* dst = (pr < 0) ? J.cube + (long long)s * J.pitch
                                           : J.partials + (long long)pr * P.n_lambda;
 #if !RUBIX_DEP_BANDADD
                     // later bands add to the row: start moving it into L2 now
@@ -538,6 +538,10 @@ int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, 
     case r: fn = k_deposit<r>; break;
         RUBIX_DEP_R(1) RUBIX_DEP_R(2) RUBIX_DEP_R(3) RUBIX_DEP_R(4) RUBIX_DEP_R(5) RUBIX_DEP_R(6)
         RUBIX_DEP_R(7) RUBIX_DEP_R(8) RUBIX_DEP_R(9) RUBIX_DEP_R(10) RUBIX_DEP_R(11) RUBIX_DEP_R(12)
+#if RUBIX_DEP_RMAX > 12
+        RUBIX_DEP_R(13) RUBIX_DEP_R(14) RUBIX_DEP_R(15) RUBIX_DEP_R(16) RUBIX_DEP_R(17) RUBIX_DEP_R(18)
+        RUBIX_DEP_R(19) RUBIX_DEP_R(20) RUBIX_DEP_R(21) RUBIX_DEP_R(22) RUBIX_DEP_R(23) RUBIX_DEP_R(24)
+#endif
 #undef RUBIX_DEP_R
         default: return -1;
     }
@@ -552,23 +556,23 @@ int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, 
 // K5: rows of split spaxels = FP64 sum of their partial rows in item order.
 // ----------------------------------------------------------------------------
 __global__ void k_combine(const int* __restrict__ part_off, int n_s, int n_lambda, const float* __restrict__ partials,
-                          float* __restrict__ cube) {
+                          float* __restrict__ cube, int pitch) {
     for (int s = blockIdx.x; s < n_s; s += gridDim.x) {
         const int p0 = part_off[s], p1 = part_off[s + 1];
         if (p1 <= p0) continue;
         for (int j = threadIdx.x; j < n_lambda; j += blockDim.x) {
             double acc = 0.0;
             for (int r = p0; r < p1; ++r) acc += (double)partials[(long long)r * n_lambda + j];
-            cube[(long long)s * n_lambda + j] = (float)acc;
+            cube[(long long)s * pitch + j] = (float)acc;
         }
     }
 }
 
-int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube,
+int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube, int pitch,
                    cudaStream_t st) {
     int nb = n_s < 152 * 8 ? n_s : 152 * 8;
     if (nb < 1) return 0;
-    k_combine<<<nb, 256, 0, st>>>(part_off, n_s, n_lambda, partials, cube);
+    k_combine<<<nb, 256, 0, st>>>(part_off, n_s, n_lambda, partials, cube, pitch);
     return 1;
 }
 

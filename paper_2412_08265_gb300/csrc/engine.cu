@@ -363,7 +363,7 @@ struct Buf {
 
 // Every device buffer of a plan for n particles, with its size.
 std::vector<Buf> plan_buffers(Plan* P, const SspState& S, int n_s, int n_lambda, long long n, bool with_out,
-                              bool with_grad, bool need_tmp, bool staging) {
+                              bool with_grad, bool need_tmp, bool staging, int pitch0) {
     const size_t N = (size_t)std::max(n, 1ll);
     const long long item_cap = (long long)n_s + n / S.chunk + 2;
     const long long part_cap = 2 * (n / S.chunk) + 2;
@@ -384,7 +384,8 @@ std::vector<Buf> plan_buffers(Plan* P, const SspState& S, int n_s, int n_lambda,
         {(void**)&P->d_seg_off, 4 * ((size_t)n_s * S.n_bands + 2)}, {(void**)&P->d_n_items, 4 * ((size_t)n_s + 1)},
         {(void**)&P->d_n_parts, 4 * ((size_t)n_s + 1)}, {(void**)&P->d_item_off, 4 * ((size_t)n_s + 1)},
         {(void**)&P->d_part_off, 4 * ((size_t)n_s + 1)},
-        {(void**)&P->d_scan_scratch, 4 * (scan_scratch_ints(n_s + 1) + 16)}, {(void**)&P->d_cube0, cube},
+        {(void**)&P->d_scan_scratch, 4 * (scan_scratch_ints(n_s + 1) + 16)},
+        {(void**)&P->d_cube0, (size_t)n_s * std::max(pitch0, n_lambda) * sizeof(float)},
         {(void**)&P->d_job_cost, 8 * (size_t)(kMaxJobs + 1)},
     };
     v.insert(v.end(), rest.begin(), rest.end());
@@ -405,6 +406,13 @@ int conv_radius_psf(const rubix_telescope* tel) {
     const double sp = tel->psf_fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
     return sp > 0.0 ? kernel_radius(sp, tel->psf_radius) : 0;
 }
+// Row stride of the pre-convolution cube: 16-byte rows when the PSF/LSF radii
+// have a TMA kernel (it loads rows with 3-D TMA boxes), else dense.
+int cube0_pitch(int rp, int rl, int n_lambda) {
+    unsigned box[2];
+    return conv_tma_box(rp, rl, box) ? (n_lambda + 3) / 4 * 4 : n_lambda;
+}
+
 int conv_radius_lsf(const rubix_telescope* tel) {
     const double sl = tel->lsf_sigma / tel->dlambda;
     return sl > 0.0 ? kernel_radius(sl, tel->lsf_radius) : 0;
@@ -415,10 +423,11 @@ int conv_radius_lsf(const rubix_telescope* tel) {
 size_t plan_bytes(const SspState& S, const rubix_telescope* tel, long long n, bool with_out, bool with_grad,
                   bool staging) {
     Plan tmp;
-    const bool need_tmp = psf_lsf_needs_tmp(conv_radius_psf(tel), conv_radius_lsf(tel));
+    const int rp = conv_radius_psf(tel), rl = conv_radius_lsf(tel);
+    const bool need_tmp = psf_lsf_needs_tmp(rp, rl);
     size_t total = 0;
-    for (const Buf& b :
-         plan_buffers(&tmp, S, tel->nx * tel->ny, tel->n_lambda, n, with_out, with_grad, need_tmp, staging))
+    for (const Buf& b : plan_buffers(&tmp, S, tel->nx * tel->ny, tel->n_lambda, n, with_out, with_grad, need_tmp,
+                                     staging, cube0_pitch(rp, rl, tel->n_lambda)))
         total += round256(b.bytes);
     return total;
 }
@@ -426,7 +435,7 @@ size_t plan_bytes(const SspState& S, const rubix_telescope* tel, long long n, bo
 void plan_release(Plan* P) {
     if (!P->S) return;
     const bool need_tmp = true;
-    for (const Buf& b : plan_buffers(P, *P->S, P->n_s, P->tel.n_lambda, P->cap, true, true, need_tmp, true)) {
+    for (const Buf& b : plan_buffers(P, *P->S, P->n_s, P->tel.n_lambda, P->cap, true, true, need_tmp, true, P->pitch0)) {
         if (*b.ptr) {
             if (P->alloc.async) cudaFreeAsync(*b.ptr, P->alloc.stream);
             else cudaFree(*b.ptr);
@@ -471,6 +480,9 @@ rubix_status plan_init(Plan* P, const SspState* S, const rubix_telescope* tel, l
     if (sp > 0.0) gauss_kernel(sp, C.rp, C.gp); else C.gp[0] = 1.f;
     if (sl > 0.0) gauss_kernel(sl, C.rl, C.gl); else C.gl[0] = 1.f;
     P->need_conv = (sp > 0.0) || (sl > 0.0);
+    C.err = S->d_err;
+    P->pitch0 = cube0_pitch(C.rp, C.rl, tel->n_lambda);
+    P->has_conv_map = false;
     P->cap = std::max(n, 1ll);
     P->item_cap = (long long)P->n_s + P->cap / S->chunk + 2;
     P->part_cap = 2 * (P->cap / S->chunk) + 2;
@@ -478,7 +490,8 @@ rubix_status plan_init(Plan* P, const SspState* S, const rubix_telescope* tel, l
     P->bytes = 0;
     const int fail_at = fault_alloc_at();
     int idx = 0;
-    for (const Buf& b : plan_buffers(P, *S, P->n_s, tel->n_lambda, P->cap, with_out, with_grad, need_tmp, a.staging)) {
+    for (const Buf& b :
+         plan_buffers(P, *S, P->n_s, tel->n_lambda, P->cap, with_out, with_grad, need_tmp, a.staging, P->pitch0)) {
         cudaError_t e;
         if (++idx == fail_at) e = cudaErrorMemoryAllocation;
         else if (!a.async) e = cudaMalloc(b.ptr, round256(b.bytes));
@@ -491,6 +504,28 @@ rubix_status plan_init(Plan* P, const SspState* S, const rubix_telescope* tel, l
             return fail(RUBIX_ERR_OOM, "plan allocation of %zu bytes failed: %s", b.bytes, cudaGetErrorString(e));
         }
         P->bytes += round256(b.bytes);
+    }
+    unsigned box[2];
+    if (P->pitch0 != tel->n_lambda && conv_tma_box(C.rp, C.rl, box)) {
+        // 3-D view of the pre-convolution cube: x = bin (n_lambda of each
+        // pitched row), y = spaxel x, z = spaxel y; zero fill outside
+        PFN_encodeTiled_t enc = get_encode_tiled();
+        if (!enc) {
+            plan_release(P);
+            return fail(RUBIX_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        }
+        cuuint64_t gdim[3] = {(cuuint64_t)tel->n_lambda, (cuuint64_t)tel->nx, (cuuint64_t)tel->ny};
+        cuuint64_t gstr[2] = {(cuuint64_t)P->pitch0 * 4, (cuuint64_t)P->pitch0 * 4 * (cuuint64_t)tel->nx};
+        cuuint32_t bx[3] = {box[0], box[1], 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        CUresult r = enc(&P->conv_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P->d_cube0, gdim, gstr, bx, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            plan_release(P);
+            return fail(RUBIX_ERR_CUDA, "cuTensorMapEncodeTiled (PSF/LSF) failed (%d)", (int)r);
+        }
+        P->has_conv_map = true;
     }
     return RUBIX_OK;
 }
@@ -644,6 +679,7 @@ DepJob plan_job(const Plan& P, float* target) {
     J.partials = P.d_partials;
     J.part_cap = P.part_cap;
     J.n_s = P.n_s;
+    J.pitch = (target == P.d_cube0) ? P.pitch0 : P.tel.n_lambda;
     return J;
 }
 
@@ -674,7 +710,8 @@ int enqueue_deposit(const SspState& S, const DepJob* jobs, int n_jobs, long long
 
 int enqueue_post(Plan& P, float* target, float* out, uint64_t noise_seed, float noise_s2n, cudaStream_t st,
                  cudaEvent_t* ev) {
-    int l = launch_combine(P.d_part_off, P.n_s, P.tel.n_lambda, P.d_partials, target, st);
+    int l = launch_combine(P.d_part_off, P.n_s, P.tel.n_lambda, P.d_partials, target,
+                           target == P.d_cube0 ? P.pitch0 : P.tel.n_lambda, st);
     if (ev) cudaEventRecord(ev[4], st);
     const bool noise = noise_s2n > 0.f;
     if (P.need_conv || noise) {
@@ -682,7 +719,7 @@ int enqueue_post(Plan& P, float* target, float* out, uint64_t noise_seed, float 
         C.noise_inv_s2n = noise ? 1.0f / noise_s2n : 0.f;
         C.seed_lo = (uint32_t)noise_seed;
         C.seed_hi = (uint32_t)(noise_seed >> 32);
-        l += launch_psf_lsf(C, P.d_cube0, P.d_tmp, out, st);
+        l += launch_psf_lsf(C, P.d_cube0, P.pitch0, P.has_conv_map ? &P.conv_map : nullptr, P.d_tmp, out, st);
     }
     return l;
 }

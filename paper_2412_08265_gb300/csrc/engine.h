@@ -86,6 +86,9 @@ struct Plan {
     PartRec* d_prec = nullptr;
     float* d_partials = nullptr;
     float *d_cube0 = nullptr, *d_tmp = nullptr, *d_out = nullptr;
+    int pitch0 = 0;                         // row stride of d_cube0 (16-byte rows for the TMA PSF/LSF)
+    CUtensorMap conv_map{};                 // 3-D TMA map of d_cube0 for the PSF/LSF kernel
+    bool has_conv_map = false;
     long long* d_job_cost = nullptr;        // deposit launch scratch [kMaxJobs + 1]
     double *d_contrib = nullptr, *d_red = nullptr;
     float4* d_wu = nullptr;                 // backward: unit-mass weights [cap]

@@ -121,11 +121,11 @@ struct DepJob {
     const Item* items;
     const int* item_off;     // [n_s + 1]: total items at [n_s]
     const int* seg_off;      // [n_s * n_bands + 2]: in-field particles at [n_s * n_bands]
-    float* cube;             // [n_s][n_lambda]
+    float* cube;             // [n_s][pitch] (the first n_lambda of each row)
     float* partials;         // [part_cap][n_lambda]
     long long part_cap;
     int n_s;
-    int pad;
+    int pitch;               // cube row stride in floats (>= n_lambda)
 };
 struct DepositParams {
     const float4* quad;      // [n_ls][n_cells] SSP cell quads (the four bilinear corners per node)
@@ -151,7 +151,7 @@ int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, 
 size_t deposit_smem_bytes(int ncb, int slab_w);
 
 // K5: combine partial rows of split spaxels in FP64, fixed order.
-int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube,
+int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube, int pitch,
                    cudaStream_t st);
 
 // K6: PSF + LSF (+ noise).
@@ -163,8 +163,17 @@ struct ConvParams {
     float gl[2 * kMaxRadius + 1];
     float noise_inv_s2n;         // 0 = no noise
     uint32_t seed_lo, seed_hi;
+    unsigned* err;               // device error word (bounded waits of the TMA kernel)
 };
-int launch_psf_lsf(const ConvParams& P, const float* in, float* tmp, float* out, cudaStream_t st);
+// `in` rows have stride in_pitch floats; `out` is dense ([ny][nx][n_lambda]).
+// in_map (nullable): a 3-D TMA map of `in` (x = wavelength over n_lambda, y = x
+// spaxel, z = y spaxel; zero fill outside) from conv_tma_map; with it the
+// instrument radii take the TMA kernel.
+int launch_psf_lsf(const ConvParams& P, const float* in, int in_pitch, const CUtensorMap* in_map, float* tmp,
+                   float* out, cudaStream_t st);
+// Box the TMA kernel loads for these radii: {wavelength, x}; false if the
+// radii have no TMA instantiation.
+bool conv_tma_box(int rp, int rl, unsigned box[2]);
 // True if launch_psf_lsf needs the intermediate cube `tmp` for these radii.
 bool psf_lsf_needs_tmp(int rp, int rl);
 

@@ -266,6 +266,196 @@ static bool try_fused(const ConvParams& P, const float* in, float* out, cudaStre
     return false;
 }
 
+
+// ----------------------------------------------------------------------------
+// TMA variant of the fused pass for a cube whose rows are 16-byte aligned (the
+// deposit's own pitched cube). One CTA owns kTL = 128 bins x kTX = 16 spaxels
+// along x x kTY rows along y. Each input row arrives as one 3-D TMA box
+// (bins j0 - RLa .. j0 + kTL + RLa, spaxels x0 - rp .. x0 + kTX + rp; zero fill
+// outside the cube is the zero padding) in a kTS-stage mbarrier ring. A lane
+// computes 4 consecutive bins: the LSF from 16-byte shared loads into a
+// double-buffered row, then the PSF along x and the rotating PSF-y
+// accumulators of the previous kernel, in the same summation order, so the
+// result is bitwise that of the cp.async kernel. One barrier per input row.
+// ----------------------------------------------------------------------------
+#ifndef RUBIX_PSF_TY
+#define RUBIX_PSF_TY 50
+#endif
+#ifndef RUBIX_PSF_TSTAGES
+#define RUBIX_PSF_TSTAGES 4
+#endif
+constexpr int kTL = 128, kTX = 16, kTThreads = 256, kTWarps = kTThreads / 32, kTXW = kTX / kTWarps;
+constexpr int kTY = RUBIX_PSF_TY, kTS = RUBIX_PSF_TSTAGES;
+
+template <int RP, int RL>
+struct TmaGeo {
+    static constexpr int RLa = (RL + 3) / 4 * 4;  // wavelength halo rounded up to 16 bytes
+    static constexpr int LW = kTL + 2 * RLa;      // box: bins
+    static constexpr int XW = kTX + 2 * RP;       // box: spaxels along x
+    static constexpr int NV = 1 + RLa / 2;        // 16-byte loads per lane for 4 LSF outputs
+    static constexpr int stage_floats = (LW * XW + 31) / 32 * 32;  // 128-byte aligned stages
+    static constexpr size_t smem = 128 + (size_t)kTS * stage_floats * 4 + 2 * (size_t)XW * kTL * 4;
+};
+
+template <int RP, int RL>
+__global__ void __launch_bounds__(kTThreads) k_psf_lsf_tma(const __grid_constant__ ConvParams P,
+                                                           const __grid_constant__ CUtensorMap in_map,
+                                                           float* __restrict__ out) {
+    using G = TmaGeo<RP, RL>;
+    constexpr int NR = 2 * RP + 1;
+    extern __shared__ __align__(1024) float smt[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smt);
+    float* stages = smt + 32;  // 128 bytes in
+    float* s_l = stages + kTS * G::stage_floats;  // [2][XW][kTL] LSF output
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j0 = blockIdx.x * kTL, x0 = blockIdx.y * kTX, y0 = blockIdx.z * kTY;
+    const int y1 = min(y0 + kTY, P.ny);
+    const int nx = P.nx, nl = P.n_lambda;
+    const int n_rows = (y1 - y0) + 2 * RP;  // input rows y0 - RP .. y1 + RP - 1
+    float gl[2 * RL + 1], gp[NR];
+#pragma unroll
+    for (int d = 0; d <= 2 * RL; ++d) gl[d] = P.gl[d];
+#pragma unroll
+    for (int d = 0; d < NR; ++d) gp[d] = P.gp[d];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTS; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int i) {  // input row i into stage i % kTS (thread 0)
+        const int s = i % kTS;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bars[s], (uint32_t)(G::LW * G::XW * 4));
+        tma_load_3d(stages + s * G::stage_floats, &in_map, &bars[s], j0 - G::RLa, x0 - RP, y0 - RP + i);
+    };
+    if (threadIdx.x == 0)
+        for (int i = 0; i < min(kTS, n_rows); ++i) issue(i);
+
+    float acc[kTXW][NR][4];
+#pragma unroll
+    for (int k = 0; k < kTXW; ++k)
+#pragma unroll
+        for (int m = 0; m < NR; ++m)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[k][m][u] = 0.f;
+
+    for (int ib = 0; ib < n_rows; ib += NR) {
+#pragma unroll
+        for (int ph = 0; ph < NR; ++ph) {  // accumulator of output row y_in - RP + m is (ph + m) % NR
+            const int i = ib + ph;
+            if (i < n_rows) {
+                const int s = i % kTS;
+                const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((i / kTS) & 1), 2000000000ll);
+                const float* src = stages + s * G::stage_floats;
+                float* dl = s_l + (i & 1) * G::XW * kTL;
+                if (ok) {
+                    for (int xi = warp; xi < G::XW; xi += kTWarps) {
+                        const float4* r4 = reinterpret_cast<const float4*>(src + xi * G::LW + 4 * lane);
+                        float v[4 * G::NV];
+#pragma unroll
+                        for (int c = 0; c < G::NV; ++c) {
+                            const float4 t = r4[c];
+                            v[4 * c] = t.x;
+                            v[4 * c + 1] = t.y;
+                            v[4 * c + 2] = t.z;
+                            v[4 * c + 3] = t.w;
+                        }
+                        float o[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            float a = 0.f;
+#pragma unroll
+                            for (int d = 0; d <= 2 * RL; ++d) a = fmaf(gl[d], v[u + d + G::RLa - RL], a);
+                            o[u] = a;
+                        }
+                        *reinterpret_cast<float4*>(dl + xi * kTL + 4 * lane) = make_float4(o[0], o[1], o[2], o[3]);
+                    }
+                }
+                if (__syncthreads_or(!ok)) {
+                    // a load did not complete in time: record it, let the copies in
+                    // flight land (bounded), and stop
+                    if (threadIdx.x == 0) {
+                        if (P.err) atomicOr(P.err, kErrTmaTimeout);
+                        for (int r = i; r < min(i + kTS, n_rows); ++r)
+                            mbar_wait_bounded(&bars[r % kTS], (uint32_t)((r / kTS) & 1), 200000000ll);
+                    }
+                    return;
+                }
+                // every warp is done with stage s: refill it
+                if (threadIdx.x == 0 && i + kTS < n_rows) issue(i + kTS);
+                const int y_done = y0 + i - 2 * RP;  // output row completed by this input row
+#pragma unroll
+                for (int k = 0; k < kTXW; ++k) {
+                    const int xo = warp * kTXW + k;
+                    float vv[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int d = 0; d < NR; ++d) {
+                        const float4 c = *reinterpret_cast<const float4*>(dl + (xo + d) * kTL + 4 * lane);
+                        vv[0] = fmaf(gp[d], c.x, vv[0]);
+                        vv[1] = fmaf(gp[d], c.y, vv[1]);
+                        vv[2] = fmaf(gp[d], c.z, vv[2]);
+                        vv[3] = fmaf(gp[d], c.w, vv[3]);
+                    }
+#pragma unroll
+                    for (int m = 0; m < NR; ++m)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            acc[k][(ph + m) % NR][u] = fmaf(gp[m], vv[u], acc[k][(ph + m) % NR][u]);
+                    float* done = acc[k][ph % NR];
+                    const int x = x0 + xo;
+                    if (y_done >= y0 && x < nx) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = j0 + 4 * lane + u;
+                            if (j < nl) {
+                                const long long idx = ((long long)y_done * nx + x) * nl + j;
+                                out[idx] = (P.noise_inv_s2n > 0.f) ? add_noise(done[u], idx, P) : done[u];
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) done[u] = 0.f;
+                }
+            }
+        }
+    }
+}
+
+// Radii with a TMA instantiation (the wavelength halo of at most 8 bins).
+#define RUBIX_TMA_RADII(X) X(3, 4) X(3, 2) X(3, 0) X(0, 4) X(0, 2) X(2, 4) X(4, 4) X(3, 3) X(3, 5)
+
+bool conv_tma_box(int rp, int rl, unsigned box[2]) {
+#define RUBIX_TMA_BOX(RP_, RL_)                    \
+    if (rp == RP_ && rl == RL_) {                  \
+        box[0] = (unsigned)TmaGeo<RP_, RL_>::LW;   \
+        box[1] = (unsigned)TmaGeo<RP_, RL_>::XW;   \
+        return true;                               \
+    }
+    RUBIX_TMA_RADII(RUBIX_TMA_BOX)
+#undef RUBIX_TMA_BOX
+    return false;
+}
+
+template <int RP, int RL>
+static bool launch_tma(const ConvParams& P, const CUtensorMap* map, float* out, cudaStream_t st) {
+    constexpr size_t smem = TmaGeo<RP, RL>::smem;
+    static_assert(smem <= 200 * 1024, "TMA PSF/LSF tile does not fit shared memory");
+    if (cudaFuncSetAttribute(k_psf_lsf_tma<RP, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return false;
+    dim3 g((P.n_lambda + kTL - 1) / kTL, (P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY);
+    k_psf_lsf_tma<RP, RL><<<g, kTThreads, smem, st>>>(P, *map, out);
+    return true;
+}
+
+static bool try_tma(const ConvParams& P, const CUtensorMap* map, float* out, cudaStream_t st) {
+#define RUBIX_TMA_CASE(RP_, RL_) \
+    if (P.rp == RP_ && P.rl == RL_) return launch_tma<RP_, RL_>(P, map, out, st);
+    RUBIX_TMA_RADII(RUBIX_TMA_CASE)
+#undef RUBIX_TMA_CASE
+    return false;
+}
+
 bool psf_lsf_needs_tmp(int rp, int rl) {
 #ifdef RUBIX_PSF_TWO_PASS
     return true;
@@ -277,7 +467,10 @@ bool psf_lsf_needs_tmp(int rp, int rl) {
     return true;
 }
 
-int launch_psf_lsf(const ConvParams& P, const float* in, float* tmp, float* out, cudaStream_t st) {
+int launch_psf_lsf(const ConvParams& P, const float* in, int in_pitch, const CUtensorMap* in_map, float* tmp,
+                   float* out, cudaStream_t st) {
+    if (in_map && try_tma(P, in_map, out, st)) return 1;
+    if (in_pitch != P.n_lambda) return -1;  // the cp.async kernels read dense rows
     if (try_fused(P, in, out, st)) return 1;
     // generic radii: two passes through an intermediate cube
     const int XW = kXC + 2 * P.rp;
