@@ -124,7 +124,8 @@ rubix_status rubix_cube_create(const rubix_ssp_grid *ssp, const rubix_telescope 
 
 /* Forward model (Sec. 3 pipeline): particles -> cube_out [ny][nx][n_lambda].
  * cube_out is a device pointer if cube_on_device = 1, else a host pointer
- * (the call then waits for the device-to-host copy). noise_s2n <= 0 turns the
+ * (the call then waits for the device-to-host copy; with page-locked memory
+ * the copy runs at the host link's rate, ~190 GB/s on GB300). noise_s2n <= 0 turns the
  * noise off; noise_seed selects the Philox stream. Deterministic: the same
  * inputs give bitwise the same cube. The sorted particle order and setup of
  * this call are kept for rubix_cube_backward.

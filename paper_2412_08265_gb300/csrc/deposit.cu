@@ -214,6 +214,39 @@ __device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g
         const int s31 = 31 * C.ncb, s30 = 30 * C.ncb;
         const float nld = -lanef * delta;
         const float d31 = 31.f * delta;
+#if RUBIX_DEP_PAIR2
+        // rounds two at a time: the per-bin arithmetic in packed FP32x2
+#pragma unroll
+        for (int r = 0; r + 1 < R; r += 2) {
+            const float4 Qa = *q;
+            const float fa = f;
+            f -= d31;
+            bool carry = f < 0.f;
+            f = carry ? f + 1.f : f;
+            q += carry ? s30 : s31;
+            const float4 Qb = *q;
+            const float fb = f;
+            f -= d31;
+            carry = f < 0.f;
+            f = carry ? f + 1.f : f;
+            q += carry ? s30 : s31;
+            const float Ma = quad_dot(w4, Qa), Mb = quad_dot(w4, Qb);
+            const float2 g = __fadd2_rn(make_float2(fa, fb), make_float2(nld, nld));
+            const float Xa = __shfl_sync(0xffffffffu, Ma, g.x < 0.f ? lane - 1 : lane + 1);
+            const float Xb = __shfl_sync(0xffffffffu, Mb, g.y < 0.f ? lane - 1 : lane + 1);
+            const float2 D = __fadd2_rn(make_float2(Xa, Xb), make_float2(-Ma, -Mb));
+            const float2 v = __ffma2_rn(make_float2(fabsf(g.x), fabsf(g.y)), D, make_float2(Ma, Mb));
+            const float2 a = __fadd2_rn(make_float2(acc[r], acc[r + 1]), v);
+            acc[r] = a.x;
+            acc[r + 1] = a.y;
+        }
+        if (R & 1) {
+            const float M = quad_dot(w4, *q);
+            const float g = f + nld;
+            const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
+            acc[R - 1] += fmaf(fabsf(g), X - M, M);
+        }
+#else
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float M = quad_dot(w4, *q);
@@ -229,6 +262,7 @@ __device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g
             f = carry ? f + 1.f : f;
             q += carry ? s30 : s31;
         }
+#endif
         return;
     }
     // general path (out of line; rare on the workloads here): each bin's node

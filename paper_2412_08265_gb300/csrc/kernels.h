@@ -38,6 +38,10 @@ constexpr int kMaxBands = 32;
 // How later age bands add to a row the first band wrote: 0 = load, add,
 // store (the row prefetched to L2 when the item starts); 1 = in-order
 // reductions at L2.
+// 1: the fast path's rounds two at a time in packed FP32x2 arithmetic.
+#ifndef RUBIX_DEP_PAIR2
+#define RUBIX_DEP_PAIR2 1
+#endif
 // Work items a warp claims at once (its first lanes look them up together).
 #ifndef RUBIX_DEP_GRAB
 #define RUBIX_DEP_GRAB 4
