@@ -191,83 +191,74 @@ __device__ __noinline__ float bin_value(const float4 w4, const float4 g4, const 
     return fmaf(f, m1 - m0, m0);
 }
 
-// Adds one particle's spectrum to acc: acc[r] of lane l (l < 31) is output bin
-// j0 + 31 r + l.
+// The rounds of one particle on the fast path: q = its slab quad at node
+// K0 + lane, f = frac(t(j0)), delta = 1 - dt/dj. acc[r] of lane l (l < 31) is
+// output bin j0 + 31 r + l.
 template <int R>
-__device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g4, const TileCtx& C,
-                                                 const float4* __restrict__ slab, const float4* __restrict__ quad,
-                                                 int lane, float lanef, float (&acc)[R],
-                                                 unsigned long long* slow_count) {
-    const int c0_bi = __float_as_int(g4.x);
-    const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
-    float f;
-    const int K0 = node_pos(C.j0, bi, g4.y, g4.z, g4.w, f);  // node position of the tile's first bin
-    const float delta = (1.f - g4.z) - g4.w;                 // 1 - dt/dj (exact up to one rounding)
-    const int kw = K0 - C.klo;
-    const int cr = cell - C.cell0;
-    // fast path (warp-uniform test): dt/dj in (1 - 1/31, 1], a cell of this
-    // band, and every node the rounds read, K0 .. K0 + 31 R, inside the slab
-    if (delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R) &&
-        (unsigned)cr < (unsigned)C.ncb) {
-        // round r: lane l reads node K0 + o_r + l, o_r = 31 r - (carries so far)
-        const float4* q = slab + (kw + lane) * C.ncb + cr;
-        const int s31 = 31 * C.ncb, s30 = 30 * C.ncb;
-        const float nld = -lanef * delta;
-        const float d31 = 31.f * delta;
+__device__ __forceinline__ void fast_rounds(const float4 w4, const float4* __restrict__ q, float f, float delta,
+                                            int ncb, int lane, float lanef, float (&acc)[R]) {
+    // round r: lane l reads node K0 + o_r + l, o_r = 31 r - (carries so far)
+    const int s31 = 31 * ncb, s30 = 30 * ncb;
+    const float nld = -lanef * delta;
+    const float d31 = 31.f * delta;
 #if RUBIX_DEP_PAIR2
-        // rounds two at a time: the per-bin arithmetic in packed FP32x2
+    // rounds two at a time: the per-bin arithmetic in packed FP32x2
 #pragma unroll
-        for (int r = 0; r + 1 < R; r += 2) {
-            const float4 Qa = *q;
-            const float fa = f;
-            f -= d31;
-            bool carry = f < 0.f;
-            f = carry ? f + 1.f : f;
-            q += carry ? s30 : s31;
-            const float4 Qb = *q;
-            const float fb = f;
-            f -= d31;
-            carry = f < 0.f;
-            f = carry ? f + 1.f : f;
-            q += carry ? s30 : s31;
-            const float Ma = quad_dot(w4, Qa), Mb = quad_dot(w4, Qb);
-            const float2 g = __fadd2_rn(make_float2(fa, fb), make_float2(nld, nld));
-            const float Xa = __shfl_sync(0xffffffffu, Ma, g.x < 0.f ? lane - 1 : lane + 1);
-            const float Xb = __shfl_sync(0xffffffffu, Mb, g.y < 0.f ? lane - 1 : lane + 1);
-            const float2 D = __fadd2_rn(make_float2(Xa, Xb), make_float2(-Ma, -Mb));
-            const float2 v = __ffma2_rn(make_float2(fabsf(g.x), fabsf(g.y)), D, make_float2(Ma, Mb));
-            const float2 a = __fadd2_rn(make_float2(acc[r], acc[r + 1]), v);
-            acc[r] = a.x;
-            acc[r + 1] = a.y;
-        }
-        if (R & 1) {
-            const float M = quad_dot(w4, *q);
-            const float g = f + nld;
-            const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
-            acc[R - 1] += fmaf(fabsf(g), X - M, M);
-        }
+    for (int r = 0; r + 1 < R; r += 2) {
+        const float4 Qa = *q;
+        const float fa = f;
+        f -= d31;
+        bool carry = f < 0.f;
+        f = carry ? f + 1.f : f;
+        q += carry ? s30 : s31;
+        const float4 Qb = *q;
+        const float fb = f;
+        f -= d31;
+        carry = f < 0.f;
+        f = carry ? f + 1.f : f;
+        q += carry ? s30 : s31;
+        const float Ma = quad_dot(w4, Qa), Mb = quad_dot(w4, Qb);
+        // bin j0 + 31 r + l sits at node K0 + o_r + l + g, g = f - l delta in
+        // (-1, 1); the neighbour node on g's side is lane l -+ 1's:
+        // value = M + |g| (M_neighbour - M)
+        const float2 g = __fadd2_rn(make_float2(fa, fb), make_float2(nld, nld));
+        const float Xa = __shfl_sync(0xffffffffu, Ma, g.x < 0.f ? lane - 1 : lane + 1);
+        const float Xb = __shfl_sync(0xffffffffu, Mb, g.y < 0.f ? lane - 1 : lane + 1);
+        const float2 D = __fadd2_rn(make_float2(Xa, Xb), make_float2(-Ma, -Mb));
+        const float2 v = __ffma2_rn(make_float2(fabsf(g.x), fabsf(g.y)), D, make_float2(Ma, Mb));
+        const float2 a = __fadd2_rn(make_float2(acc[r], acc[r + 1]), v);
+        acc[r] = a.x;
+        acc[r + 1] = a.y;
+    }
+    if (R & 1) {
+        const float M = quad_dot(w4, *q);
+        const float g = f + nld;
+        const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
+        acc[R - 1] += fmaf(fabsf(g), X - M, M);
+    }
 #else
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float M = quad_dot(w4, *q);
-            // bin j0 + 31 r + l sits at node K0 + o_r + l + g, g = f - l delta in
-            // (-1, 1); the neighbour node on g's side is lane l -+ 1's:
-            // value = M + |g| (M_neighbour - M)
-            const float g = f + nld;
-            const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
-            acc[r] += fmaf(fabsf(g), X - M, M);
-            // the next round starts 31 dt/dj = 31 - 31 delta nodes further on
-            f -= d31;
-            const bool carry = f < 0.f;
-            f = carry ? f + 1.f : f;
-            q += carry ? s30 : s31;
-        }
-#endif
-        return;
+    for (int r = 0; r < R; ++r) {
+        const float M = quad_dot(w4, *q);
+        const float g = f + nld;
+        const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
+        acc[r] += fmaf(fabsf(g), X - M, M);
+        // the next round starts 31 dt/dj = 31 - 31 delta nodes further on
+        f -= d31;
+        const bool carry = f < 0.f;
+        f = carry ? f + 1.f : f;
+        q += carry ? s30 : s31;
     }
-    // general path (out of line; rare on the workloads here): each bin's node
-    // pair from the slab if every bin of the warp is inside it, else from the
-    // global quad array
+#endif
+}
+
+// General path (out of line; rare on the workloads here): each bin's node
+// pair from the slab if every bin of the warp is inside it, else from the
+// global quad array.
+template <int R>
+__device__ __forceinline__ void general_particle(const float4 w4, const float4 g4, const TileCtx& C,
+                                                 const float4* __restrict__ slab, const float4* __restrict__ quad,
+                                                 int lane, float (&acc)[R], unsigned long long* slow_count) {
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < R; ++i) ok = ok && bin_in_slab(g4, C, C.j0 + 31 * i + lane, lane);
@@ -277,51 +268,35 @@ __device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g
     for (int i = 0; i < R; ++i) acc[i] += bin_value(w4, g4, C, C.j0 + 31 * i + lane, lane, use_slab, slab, quad);
 }
 
-// Fast-path test and per-particle state of the interleaved pair path.
-struct FastState {
-    const float4* q;  // slab quad of node K0 + lane
-    float f, nld, d31;
-};
+// Fast-path setup of one particle for this tile and band: the slab offset of
+// its cell at node K0 (without the lane), frac(t(j0)) and 1 - dt/dj; false
+// if it takes the general path (dt/dj outside (1 - 1/31, 1], a cell of
+// another band, or a node of the rounds, K0 .. K0 + 31 R, outside the slab).
 template <int R>
-__device__ __forceinline__ bool fast_setup(const float4 g4, const TileCtx& C, const float4* __restrict__ slab,
-                                           int lane, float lanef, FastState& S) {
+__device__ __forceinline__ bool fast_setup(const float4 g4, const TileCtx& C, int& base, float& f, float& delta) {
     const int c0_bi = __float_as_int(g4.x);
     const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
-    const int K0 = node_pos(C.j0, bi, g4.y, g4.z, g4.w, S.f);
-    const float delta = (1.f - g4.z) - g4.w;
+    const int K0 = node_pos(C.j0, bi, g4.y, g4.z, g4.w, f);  // node position of the tile's first bin
+    delta = (1.f - g4.z) - g4.w;                             // 1 - dt/dj (exact up to one rounding)
     const int kw = K0 - C.klo;
     const int cr = cell - C.cell0;
-    S.q = slab + (kw + lane) * C.ncb + cr;
-    S.nld = -lanef * delta;
-    S.d31 = 31.f * delta;
+    base = kw * C.ncb + cr;
     return delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R) &&
            (unsigned)cr < (unsigned)C.ncb;
 }
 
-// Two particles of one item at once (both on the fast path): two independent
-// dependency chains per round, one accumulator update for both.
+// Adds one particle's spectrum to acc (setup by every lane; warp-uniform path).
 template <int R>
-__device__ __forceinline__ void deposit_pair(const float4 wa, FastState A, const float4 wb, FastState B,
-                                             const TileCtx& C, int lane, float (&acc)[R]) {
-    const int s31 = 31 * C.ncb, s30 = 30 * C.ncb;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const float Ma = quad_dot(wa, *A.q);
-        const float Mb = quad_dot(wb, *B.q);
-        const float ga = A.f + A.nld, gb = B.f + B.nld;
-        const float Xa = __shfl_sync(0xffffffffu, Ma, ga < 0.f ? lane - 1 : lane + 1);
-        const float Xb = __shfl_sync(0xffffffffu, Mb, gb < 0.f ? lane - 1 : lane + 1);
-        const float va = fmaf(fabsf(ga), Xa - Ma, Ma);
-        const float vb = fmaf(fabsf(gb), Xb - Mb, Mb);
-        acc[r] += va + vb;
-        A.f -= A.d31;
-        B.f -= B.d31;
-        const bool ca = A.f < 0.f, cb = B.f < 0.f;
-        A.f = ca ? A.f + 1.f : A.f;
-        B.f = cb ? B.f + 1.f : B.f;
-        A.q += ca ? s30 : s31;
-        B.q += cb ? s30 : s31;
-    }
+__device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g4, const TileCtx& C,
+                                                 const float4* __restrict__ slab, const float4* __restrict__ quad,
+                                                 int lane, float lanef, float (&acc)[R],
+                                                 unsigned long long* slow_count) {
+    int base;
+    float f, delta;
+    if (fast_setup<R>(g4, C, base, f, delta))
+        fast_rounds<R>(w4, slab + base + lane * C.ncb, f, delta, C.ncb, lane, lanef, acc);
+    else
+        general_particle<R>(w4, g4, C, slab, quad, lane, acc, slow_count);
 }
 
 // Per-tile cost of each job (in-field particles + cost_c0 per work item) and
@@ -344,10 +319,6 @@ constexpr int kJobChunk = 32;  // jobs per shared-memory work table
 // one prefetched into L1.
 #ifndef RUBIX_DEP_RECPF
 #define RUBIX_DEP_RECPF 2
-#endif
-// 1: consecutive particles of an item are deposited two at a time.
-#ifndef RUBIX_DEP_PAIRP
-#define RUBIX_DEP_PAIRP 0
 #endif
 
 template <int R>
@@ -493,28 +464,7 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_c
                     float acc[R];
 #pragma unroll
                     for (int r = 0; r < R; ++r) acc[r] = 0.f;
-#if RUBIX_DEP_PAIRP
-                    int q = q0;
-                    for (; q + 1 < q1; q += 2) {
-                        if (q + 2 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * (q + 2)));
-                        if (q + 3 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * (q + 3)));
-                        const float4 wa = rec4[2 * q], ga4 = rec4[2 * q + 1];
-                        const float4 wb = rec4[2 * q + 2], gb4 = rec4[2 * q + 3];
-                        FastState A, B;
-                        const bool fa = fast_setup<R>(ga4, C, slab, lane, lanef, A);
-                        const bool fb = fast_setup<R>(gb4, C, slab, lane, lanef, B);
-                        if (fa && fb) {
-                            deposit_pair<R>(wa, A, wb, B, C, lane, acc);
-                        } else {
-                            deposit_particle<R>(wa, ga4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
-                            deposit_particle<R>(wb, gb4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
-                        }
-                    }
-                    if (q < q1) {
-                        const float4 w4 = rec4[2 * q], g4 = rec4[2 * q + 1];
-                        deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
-                    }
-#elif RUBIX_DEP_RECPF == 2
+#if RUBIX_DEP_RECPF == 2
                     // the next particle's record is pulled into L1 while the current
                     // one is deposited (no registers held across the particle)
                     if (q0 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * q0));
