@@ -124,8 +124,55 @@ __device__ __forceinline__ AdjSums adj_particle(const float4 w, const float4 g4,
     const float d31 = 31.f * delta;
     float tb = ((float)K0 + lanef) + ls0_over;  // absolute node position of lane l's node, / dls
     AdjSums S{0.f, 0.f, 0.f, 0.f};
+#if RUBIX_DEP_PAIR2
+    // dS/dta and dS/dtz as quad dot products with the weight vectors a and b;
+    // rounds two at a time, partial sums in packed FP32x2 (one lane per round)
+    const float4 wa = make_float4(-s01, s01, -s23, s23), wb = make_float4(-s02, -s13, s02, s13);
+    float2 sm2 = make_float2(0.f, 0.f), sa2 = sm2, sz2 = sm2, sv2 = sm2;
+#pragma unroll
+    for (int r = 0; r + 1 < R; r += 2) {
+        const float4 Qa = *q;
+        const float fa = f, ta = tb;
+        f -= d31;
+        bool carry = f < 0.f;
+        f = carry ? f + 1.f : f;
+        q += carry ? s30 : s31;
+        tb += carry ? 30.f : 31.f;
+        const float4 Qb = *q;
+        const float fb = f, tbb = tb;
+        f -= d31;
+        carry = f < 0.f;
+        f = carry ? f + 1.f : f;
+        q += carry ? s30 : s31;
+        tb += carry ? 30.f : 31.f;
+        const float2 M = make_float2(quad_dot(w, Qa), quad_dot(w, Qb));
+        const float2 A = make_float2(quad_dot(wa, Qa), quad_dot(wa, Qb));
+        const float2 B = make_float2(quad_dot(wb, Qa), quad_dot(wb, Qb));
+        const float2 g = __fadd2_rn(make_float2(fa, fb), make_float2(nld, nld));
+        const int srca = g.x < 0.f ? lane - 1 : lane + 1, srcb = g.y < 0.f ? lane - 1 : lane + 1;
+        const float2 XM = make_float2(__shfl_sync(0xffffffffu, M.x, srca), __shfl_sync(0xffffffffu, M.y, srcb));
+        const float2 XA = make_float2(__shfl_sync(0xffffffffu, A.x, srca), __shfl_sync(0xffffffffu, A.y, srcb));
+        const float2 XB = make_float2(__shfl_sync(0xffffffffu, B.x, srca), __shfl_sync(0xffffffffu, B.y, srcb));
+        const float2 ag = make_float2(fabsf(g.x), fabsf(g.y));
+        const float2 G2 = make_float2(G[r], G[r + 1]);
+        const float2 dM = __fadd2_rn(XM, make_float2(-M.x, -M.y));
+        sm2 = __ffma2_rn(G2, __ffma2_rn(ag, dM, M), sm2);
+        sa2 = __ffma2_rn(G2, __ffma2_rn(ag, __fadd2_rn(XA, make_float2(-A.x, -A.y)), A), sa2);
+        sz2 = __ffma2_rn(G2, __ffma2_rn(ag, __fadd2_rn(XB, make_float2(-B.x, -B.y)), B), sz2);
+        // slope between the bracketing nodes, times the bin's node position
+        const float2 sl = make_float2(g.x < 0.f ? -dM.x : dM.x, g.y < 0.f ? -dM.y : dM.y);
+        sv2 = __ffma2_rn(__fmul2_rn(G2, sl), __fadd2_rn(make_float2(ta, tbb), g), sv2);
+    }
+    S.sm = sm2.x + sm2.y;
+    S.sa = sa2.x + sa2.y;
+    S.sz = sz2.x + sz2.y;
+    S.sv = sv2.x + sv2.y;
+#pragma unroll
+    for (int r = R & ~1; r < R; ++r) {
+#else
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+#endif
         const float4 Q = *q;
         const float M = quad_dot(w, Q);
         const float A = s01 * (Q.y - Q.x) + s23 * (Q.w - Q.z);

@@ -284,6 +284,9 @@ static bool try_fused(const ConvParams& P, const float* in, float* out, cudaStre
 #ifndef RUBIX_PSF_TSTAGES
 #define RUBIX_PSF_TSTAGES 4
 #endif
+#ifndef RUBIX_PSF_TMINB
+#define RUBIX_PSF_TMINB 2       // CTAs per SM the register budget is sized for
+#endif
 constexpr int kTL = 128, kTX = 16, kTThreads = 256, kTWarps = kTThreads / 32, kTXW = kTX / kTWarps;
 constexpr int kTY = RUBIX_PSF_TY, kTS = RUBIX_PSF_TSTAGES;
 
@@ -298,7 +301,7 @@ struct TmaGeo {
 };
 
 template <int RP, int RL>
-__global__ void __launch_bounds__(kTThreads) k_psf_lsf_tma(const __grid_constant__ ConvParams P,
+__global__ void __launch_bounds__(kTThreads, RUBIX_PSF_TMINB) k_psf_lsf_tma(const __grid_constant__ ConvParams P,
                                                            const __grid_constant__ CUtensorMap in_map,
                                                            float* __restrict__ out) {
     using G = TmaGeo<RP, RL>;
