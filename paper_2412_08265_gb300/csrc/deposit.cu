@@ -322,7 +322,7 @@ constexpr int kJobChunk = 32;  // jobs per shared-memory work table
 #endif
 
 template <int R>
-__global__ void __launch_bounds__(RUBIX_DEP_THREADS, 1) k_deposit(const __grid_constant__ DepositParams P,
+__global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_deposit(const __grid_constant__ DepositParams P,
                                                                    const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);

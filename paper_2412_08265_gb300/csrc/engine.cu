@@ -275,7 +275,12 @@ rubix_status ssp_state_create(const rubix_ssp_grid* ssp, const rubix_telescope* 
     const double v_halo = RUBIX_DEP_VHALO;
     const double lam_max = (tel->lambda0 + (tel->n_lambda - 1) * tel->dlambda) / (1.0 + tel->z_cosmo);
     const int shift = (int)std::ceil(lam_max / S.dls * (v_halo / kC_kms) / (1.0 - v_halo / kC_kms));
-    const long long budget = (long long)h->smem_optin - kDepHeader;
+    long long budget = (long long)h->smem_optin - kDepHeader;
+    if (RUBIX_DEP_CTAS > 1) {
+        int per_sm = 0;
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+        budget = std::min<long long>(budget, per_sm / RUBIX_DEP_CTAS - 1024 - kDepHeader);  // 1 KB reserved per CTA
+    }
     struct Geo { int apb, bands, ncb, box_w, n_boxes, slab_w, R; double cost; };
     Geo best{0, 0, 0, 0, 0, 0, 0, 1e300};
     const bool fast_A = A0 <= 1.0 && A0 > 1.0 - 1.0 / 31.0;
@@ -331,7 +336,7 @@ rubix_status ssp_state_create(const rubix_ssp_grid* ssp, const rubix_telescope* 
     if ((h->box_w * h->ncb * (int)sizeof(float4)) % 128 != 0)
         return bail(fail(RUBIX_ERR_CUDA, "internal: TMA box of %d x %d quads is not 128-byte aligned", h->box_w, h->ncb));
     h->dep_smem = deposit_smem_bytes(h->ncb, h->slab_w);
-    h->dep_ctas = h->n_sm;
+    h->dep_ctas = h->n_sm * RUBIX_DEP_CTAS;
     if (h->slab_w > 0) {
         PFN_encodeTiled_t enc = get_encode_tiled();
         if (!enc) return bail(fail(RUBIX_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"));

@@ -19,6 +19,10 @@ constexpr int kMaxBands = 32;
 #ifndef RUBIX_DEP_THREADS
 #define RUBIX_DEP_THREADS 896
 #endif
+// Deposit CTAs resident per SM (each gets 1/RUBIX_DEP_CTAS of the shared memory).
+#ifndef RUBIX_DEP_CTAS
+#define RUBIX_DEP_CTAS 1
+#endif
 // Deposit geometry: particles per work item, the line-of-sight speed (km/s)
 // the shared-memory slab's Doppler halo covers, the most 31-bin rounds per
 // wavelength tile, and a fixed number of age bands (0 = chosen by the cost
