@@ -209,8 +209,10 @@ def run_reference(args):
 SERVE_SPAXEL_KPC = 0.2
 
 
-def _drive(torch, srv, dev, reqs, ins, arrivals):
+def _drive(torch, srv, dev, reqs, ins, arrivals, max_outstanding=48):
     """Submit request i at arrivals[i] seconds (host clock), poll to completion.
+    The client holds at most max_outstanding requests (and their output cubes)
+    at a time; a later submit still counts its latency from its arrival time.
     Returns per-request latency (arrival -> completion, s) and the makespan."""
     from paper_2412_08265_gb300 import capi, synth
     n = len(reqs)
@@ -221,7 +223,7 @@ def _drive(torch, srv, dev, reqs, ins, arrivals):
     i = 0
     while i < n or pend:
         now = time.perf_counter()
-        while i < n and now >= t0 + arrivals[i]:
+        while i < n and now >= t0 + arrivals[i] and len(pend) < max_outstanding:
             tel = synth.serving_telescope(reqs[i]["side"])
             out = torch.empty((tel.ny, tel.nx, tel.n_lambda), dtype=torch.float32, device=dev)
             t_sub = time.perf_counter()
@@ -535,7 +537,7 @@ def main():
                     help="particles of the mid-size galaxy (smaller only for profiler captures)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the differentiable-step and large-galaxy measurements")
-    ap.add_argument("--serve-requests", type=int, default=400,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests in the serving stream (0 = no serving run)")
     ap.add_argument("--serve-load", type=float, default=0.9,
                     help="Poisson arrival rate as a fraction of the sequential path's capacity")
