@@ -221,3 +221,35 @@ def test_empty_request_and_destroy_with_pending(env):
         srv.submit(tl, dev(torch, p), torch.empty((tl.ny, tl.nx, tl.n_lambda), device="cuda"))
     srv.close()
     torch.cuda.synchronize()
+
+
+def test_concurrent_client_threads(env):
+    """Four client threads submit and wait at once: every cube equals the
+    cube of the same request run alone, bitwise."""
+    import threading
+    torch, ssp = env
+    reqs = requests(12, seed=31, n_hi=1e5, side_hi=48)
+    srv = server(ssp, slots=1, batch=1)
+    alone = [run_all(torch, srv, [r])[0][0] for r in reqs]
+    srv.close()
+    srv = server(ssp, slots=8, batch=8)
+    ins = [dev(torch, p) for p, _ in reqs]
+    outs = [torch.full((t.ny, t.nx, t.n_lambda), float("nan"), device="cuda") for _, t in reqs]
+    torch.cuda.synchronize()
+    status = [None] * len(reqs)
+
+    def client(k):
+        for i in range(k, len(reqs), 4):
+            t = srv.submit(reqs[i][1], ins[i], outs[i])
+            status[i] = srv.wait(t, 120.0)
+
+    th = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert all(s == 0 for s in status)
+    assert srv.stats()["ok"] == len(reqs)
+    srv.close()
+    for a, o in zip(alone, outs):
+        assert np.array_equal(a.view(np.uint32), o.cpu().numpy().view(np.uint32))
