@@ -279,7 +279,7 @@ static bool try_fused(const ConvParams& P, const float* in, float* out, cudaStre
 // result is bitwise that of the cp.async kernel. One barrier per input row.
 // ----------------------------------------------------------------------------
 #ifndef RUBIX_PSF_TY
-#define RUBIX_PSF_TY 50
+#define RUBIX_PSF_TY 150
 #endif
 #ifndef RUBIX_PSF_TSTAGES
 #define RUBIX_PSF_TSTAGES 4
