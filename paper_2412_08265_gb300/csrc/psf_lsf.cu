@@ -239,13 +239,10 @@ template <int RP, int RL>
 static bool launch_fused(const ConvParams& P, const float* in, float* out, cudaStream_t st) {
     constexpr size_t smem = fused_smem_bytes<RP, RL>();
     static_assert(smem <= 200 * 1024, "fused PSF/LSF tile does not fit shared memory");
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_psf_lsf_fused<RP, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return false;
-        attr = true;
-    }
+    // per launch: the attribute belongs to the current device
+    if (cudaFuncSetAttribute(k_psf_lsf_fused<RP, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return false;
     dim3 g((P.n_lambda + kFL - 1) / kFL, (P.nx + kFX - 1) / kFX, (P.ny + kFY - 1) / kFY);
     k_psf_lsf_fused<RP, RL><<<g, kFThreads, smem, st>>>(P, in, out);
     return true;
@@ -478,11 +475,7 @@ int launch_psf_lsf(const ConvParams& P, const float* in, int in_pitch, const CUt
     // generic radii: two passes through an intermediate cube
     const int XW = kXC + 2 * P.rp;
     const size_t smem = (size_t)XW * (kLC + 2 * P.rl + kLC) * sizeof(float);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_lsf_psfx, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_done = true;
-    }
+    cudaFuncSetAttribute(k_lsf_psfx, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     dim3 g1((P.n_lambda + kLC - 1) / kLC, (P.nx + kXC - 1) / kXC, P.ny);
     k_lsf_psfx<<<g1, 256, smem, st>>>(P, in, tmp);
     const long long plane = (long long)P.nx * P.n_lambda;
