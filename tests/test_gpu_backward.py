@@ -118,3 +118,16 @@ def test_autograd_function(torch_cuda):
     for g, o in zip((mass.grad, age.grad, Z.grad, v.grad), ref):
         assert float(np.abs(g.cpu().numpy() - o).max()) <= 2 * TOL * float(np.abs(o).max())
     model.close()
+
+
+@pytest.mark.parametrize("z", [0.005, 0.02])
+def test_backward_redshifted_and_scaled(torch_cuda, z):
+    """Galaxy at redshift z with a flux scale: z = 0.005 keeps the deposit's
+    fast path (dt/dj > 30/31), z = 0.02 takes the general path."""
+    base = synth.mid_galaxy(n=40_000, seed=8)
+    tel = synth.Telescope(nx=24, ny=24, spaxel_size=0.5, n_lambda=3721, lambda0=4750.0, dlambda=1.25,
+                          z_cosmo=z, flux_scale=3e-3)
+    wl = synth.Workload("mid-redshifted", base.particles, base.ssp, tel)
+    rng = np.random.default_rng(11)
+    G = rng.standard_normal((tel.ny, tel.nx, tel.n_lambda))
+    _grad_check(torch_cuda, wl, G)

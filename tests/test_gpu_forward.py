@@ -390,3 +390,21 @@ def test_noise_statistics_and_reproducibility(torch_cuda):
     assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / n)
     assert stats.kstest(z[:200_000], "norm").pvalue > 1e-3
     model.close()
+
+
+@pytest.mark.parametrize("z", [0.005, 0.02])
+def test_forward_redshifted_and_scaled(torch_cuda, z):
+    """Cosmological redshift and flux scale against the oracle; z = 0.005 keeps
+    the fast path, z = 0.02 (dt/dj < 30/31) runs every bin on the general path."""
+    base = synth.mid_galaxy(n=60_000, seed=9)
+    tel = synth.Telescope(nx=24, ny=24, spaxel_size=0.5, n_lambda=3721, lambda0=4750.0, dlambda=1.25,
+                          z_cosmo=z, flux_scale=3e-3)
+    model = make_model(base.ssp, tel, n=base.particles.n)
+    got = model.forward(base.particles).cpu().numpy()
+    ref = oracle.forward(base.particles, base.ssp, tel, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_F32
+    st = model.stats()
+    assert st["device_error"] == 0
+    if z == 0.005:
+        assert st["slow_particle_tiles"] == 0
+    model.close()

@@ -198,6 +198,23 @@ def test_deposit_matches_brute_force():
     assert (bf.reshape(-1, tel.n_lambda).sum(1) > 0).sum() >= 10
 
 
+def test_redshift_and_flux_scale_match_brute_force():
+    """A galaxy at cosmological redshift z with a flux scale (distance
+    dimming): rest wavelength lambda_j / ((1 + z)(1 + v/c)), spectrum times
+    flux_scale; and flux_scale enters linearly."""
+    ssp = tiny_ssp()
+    tel = tiny_tel(psf_fwhm=0.0, lsf_sigma=0.0, z_cosmo=0.03, flux_scale=2.5e-3)
+    p = tiny_particles(n=60)
+    got = oracle.forward_parts(p, ssp, tel, n_threads=2)["cube0"]
+    bf = brute.cube0(p, ssp, tel)
+    np.testing.assert_allclose(got, bf, rtol=1e-11, atol=1e-11 * bf.max())
+    one = oracle.forward_parts(p, ssp, tiny_tel(psf_fwhm=0.0, lsf_sigma=0.0, z_cosmo=0.03), n_threads=2)["cube0"]
+    np.testing.assert_allclose(got, 2.5e-3 * one, rtol=1e-13, atol=0)
+    # the redshift moves the spectrum: z = 0 differs
+    z0 = oracle.forward_parts(p, ssp, tiny_tel(psf_fwhm=0.0, lsf_sigma=0.0), n_threads=2)["cube0"]
+    assert np.abs(z0 - one).max() > 1e-3 * np.abs(one).max()
+
+
 def test_threads_do_not_change_values():
     ssp, tel = tiny_ssp(), tiny_tel()
     p = tiny_particles(n=200)
