@@ -106,7 +106,8 @@ def _ssp_args(ssp, spectra=None):
 
 def _tel_args(tel):
     return [C.c_int(tel.nx), C.c_int(tel.ny), C.c_int(tel.n_lambda), C.c_double(tel.lambda0),
-            C.c_double(tel.dlambda), C.c_double(tel.z_cosmo), C.c_double(tel.flux_scale)]
+            C.c_double(tel.dlambda), C.c_double(tel.z_cosmo), C.c_double(tel.flux_scale),
+            C.c_int(int(getattr(tel, "resample", 0)))]
 
 
 def deposit(key, v, p, ssp, tel, mask=None, n_threads=None, spectra=None):

@@ -138,6 +138,7 @@ typedef struct {
 typedef struct {
     int nx, ny, n_l;
     double l0, dl, z_cosmo, flux_scale;
+    int resample; /* 0: value at the bin centre; 1: mean over the bin (flux-conserving) */
 } or_tel;
 
 /* Template value with zero extension outside the SSP wavelength range. */
@@ -204,13 +205,90 @@ static void or_corner_values(const or_ssp *S, const or_part *P, int64_t k, doubl
     }
 }
 
+/* ---------------------------------------------------------------------- */
+/* a5, flux-conserving alternative (resample = 1; the paper names only an  */
+/* "additional resampling", Sec. 3). Reading: output bin j covers the      */
+/* observed interval [lambda_j - dl/2, lambda_j + dl/2], and its value is  */
+/* the mean of the shifted spectrum over that interval. With the shift a  */
+/* plain scaling of wavelength, this is the mean of the rest-frame         */
+/* template over [ta, tb] (node units),                                    */
+/*   ta = ((lambda_j - dl/2)/dop - ls0)/dls,  tb = ((lambda_j + dl/2)/dop - ls0)/dls, */
+/* where the template between nodes is the same zero-extended linear       */
+/* interpolant as above. Summed over the bins, value x width then equals   */
+/* the integral of the shifted spectrum over the grid: flux is conserved.  */
+/* ---------------------------------------------------------------------- */
+
+/* Weighted template sum_c wc[c] T_c[k] at one node (zero outside). */
+static double or_node_mix(const or_ssp *S, const or_part *P, const double wc[4], int64_t k)
+{
+    int ia[4] = {P->ia, P->ia1, P->ia, P->ia1};
+    int iz[4] = {P->iz, P->iz, P->iz1, P->iz1};
+    double s = 0.0;
+    for (int c = 0; c < 4; ++c) s += wc[c] * or_T(S, ia[c], iz[c], k);
+    return s;
+}
+
+/* Linear interpolant of the weighted template at node position t. */
+static double or_mix_at(const or_ssp *S, const or_part *P, const double wc[4], double t)
+{
+    double fk = floor(t);
+    int64_t k = (int64_t)fk;
+    double f = t - fk;
+    double m0 = or_node_mix(S, P, wc, k), m1 = or_node_mix(S, P, wc, k + 1);
+    return (1.0 - f) * m0 + f * m1;
+}
+
+/* Rest-frame node positions of the two edges of output bin j. */
+static void or_bin_edges(const or_ssp *S, const or_tel *T, const or_part *P, int j,
+                         double *ta, double *tb, double *lra, double *lrb)
+{
+    double la = T->l0 + ((double)j - 0.5) * T->dl;
+    double lb = T->l0 + ((double)j + 0.5) * T->dl;
+    *lra = la / P->dop;
+    *lrb = lb / P->dop;
+    *ta = (*lra - S->ls0) / S->dls;
+    *tb = (*lrb - S->ls0) / S->dls;
+}
+
+/* Mean of the weighted template's interpolant over [ta, tb]: the integral  */
+/* segment by segment (the midpoint value of a linear piece times its      */
+/* length is its exact integral), divided by tb - ta. Segments [k, k+1]     */
+/* with k < -1 or k >= n_ls are zero and skipped.                          */
+static double or_mix_mean(const or_ssp *S, const or_part *P, const double wc[4], double ta,
+                          double tb)
+{
+    double k_lo = floor(ta), k_hi = floor(tb);
+    if (k_lo < -1.0) k_lo = -1.0;
+    if (k_hi > (double)S->n_ls - 1.0) k_hi = (double)S->n_ls - 1.0;
+    double s = 0.0;
+    for (double kd = k_lo; kd <= k_hi; kd += 1.0) {
+        int64_t k = (int64_t)kd;
+        double u0 = ta > kd ? ta : kd, u1 = tb < kd + 1.0 ? tb : kd + 1.0;
+        if (!(u1 > u0)) continue;
+        double m0 = or_node_mix(S, P, wc, k), m1 = or_node_mix(S, P, wc, k + 1);
+        double mid = 0.5 * (u0 + u1) - kd;
+        s += (u1 - u0) * (m0 + (m1 - m0) * mid);
+    }
+    return s / (tb - ta);
+}
+
 /* Spectrum of one particle on the output grid (a4 + a5 + mass scaling):  */
-/*   S_p(j) = flux_scale * m_p * sum_c w_c V_c(j).                         */
+/*   S_p(j) = flux_scale * m_p * sum_c w_c V_c(j),                         */
+/* V_c(j) the corner template at bin j's centre (resample = 0) or its mean */
+/* over bin j (resample = 1).                                              */
 int or_particle_spectrum(const or_ssp *S, const or_tel *T, double mass, double age,
                          double Z, double v, double *out)
 {
     or_part P;
     or_particle_setup(S, T, age, Z, v, &P);
+    if (T->resample) {
+        for (int j = 0; j < T->n_l; ++j) {
+            double ta, tb, lra, lrb;
+            or_bin_edges(S, T, &P, j, &ta, &tb, &lra, &lrb);
+            out[j] = T->flux_scale * mass * or_mix_mean(S, &P, P.w, ta, tb);
+        }
+        return 0;
+    }
     for (int j = 0; j < T->n_l; ++j) {
         int64_t k; double f, lr, V[4], a[4], b[4];
         or_bin_position(S, T, &P, j, &k, &f, &lr);
@@ -289,10 +367,10 @@ int or_deposit(int64_t n, const int32_t *key, const double *v, const float *mass
                int n_age, int n_Z, int n_ls, const double *la_nodes, const double *lz_nodes,
                double ls0, double dls, const double *spectra,
                int nx, int ny, int n_l, double l0, double dl, double z_cosmo, double flux_scale,
-               const uint8_t *mask, int n_threads, double *cube)
+               int resample, const uint8_t *mask, int n_threads, double *cube)
 {
     or_ssp S = {n_age, n_Z, n_ls, la_nodes, lz_nodes, ls0, dls, spectra};
-    or_tel T = {nx, ny, n_l, l0, dl, z_cosmo, flux_scale};
+    or_tel T = {nx, ny, n_l, l0, dl, z_cosmo, flux_scale, resample};
     memset(cube, 0, sizeof(double) * (size_t)nx * ny * n_l);
     or_dep_job jobs[256];
     if (n_threads > 256) n_threads = 256;
@@ -498,6 +576,30 @@ static void *or_grad_worker(void *arg)
         const double *g = J->G0 + (int64_t)s * T->n_l;
         double sm = 0.0, sla = 0.0, slz = 0.0, sv = 0.0;
         double vfac = 1.0 + J->v[p] / OR_C_KMS;
+        if (T->resample) {
+            /* bin means: S_j is linear in the corner means R_c; d/dv moves   */
+            /* both edges, d/dtb of the integral is the interpolant at tb     */
+            static const double e[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+            for (int j = 0; j < T->n_l; ++j) {
+                double ta, tb, lra, lrb, R[4];
+                or_bin_edges(S, T, &P, j, &ta, &tb, &lra, &lrb);
+                for (int c = 0; c < 4; ++c) R[c] = or_mix_mean(S, &P, e[c], ta, tb);
+                double Sj = 0.0;
+                for (int c = 0; c < 4; ++c) Sj += P.w[c] * R[c];
+                double ga = (1.0 - P.tz) * (R[1] - R[0]) + P.tz * (R[3] - R[2]);
+                double gz = (1.0 - P.ta) * (R[2] - R[0]) + P.ta * (R[3] - R[1]);
+                double dta = -lra / (S->dls * OR_C_KMS * vfac);
+                double dtb = -lrb / (S->dls * OR_C_KMS * vfac);
+                double w = tb - ta;
+                double dS = (or_mix_at(S, &P, P.w, tb) * dtb - or_mix_at(S, &P, P.w, ta) * dta) / w
+                            - Sj * (dtb - dta) / w;
+                sm += g[j] * Sj;
+                sla += g[j] * ga;
+                slz += g[j] * gz;
+                sv += g[j] * dS;
+            }
+        }
+        if (!T->resample)
         for (int j = 0; j < T->n_l; ++j) {
             int64_t k; double f, lr, V[4], a[4], b[4];
             or_bin_position(S, T, &P, j, &k, &f, &lr);
@@ -526,10 +628,11 @@ int or_gradient(int64_t n, const int32_t *key, const double *v, const float *mas
                 int n_age, int n_Z, int n_ls, const double *la_nodes, const double *lz_nodes,
                 double ls0, double dls, const double *spectra,
                 int nx, int ny, int n_l, double l0, double dl, double z_cosmo, double flux_scale,
-                const double *G0, int n_threads, double *dm, double *dage, double *dZ, double *dv)
+                int resample, const double *G0, int n_threads, double *dm, double *dage, double *dZ,
+                double *dv)
 {
     or_ssp S = {n_age, n_Z, n_ls, la_nodes, lz_nodes, ls0, dls, spectra};
-    or_tel T = {nx, ny, n_l, l0, dl, z_cosmo, flux_scale};
+    or_tel T = {nx, ny, n_l, l0, dl, z_cosmo, flux_scale, resample};
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
     or_grad_job jobs[256];

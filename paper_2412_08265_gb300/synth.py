@@ -107,7 +107,10 @@ class Telescope:
     view centred on the origin. Output wavelength bins have centres
     ``lambda0 + j*dlambda`` (j = 0..n_lambda-1). The PSF is a Gaussian of
     FWHM ``psf_fwhm`` spaxels and the LSF a Gaussian of standard deviation
-    ``lsf_sigma`` Angstrom; a radius <= 0 means ceil(4 sigma).
+    ``lsf_sigma`` Angstrom; a radius <= 0 means ceil(4 sigma). ``resample``
+    0 takes each bin's value at its centre (linear interpolation), 1 the mean
+    over the bin ``[lambda_j - dlambda/2, lambda_j + dlambda/2]``
+    (flux-conserving rebinning).
     """
 
     nx: int
@@ -122,6 +125,7 @@ class Telescope:
     lsf_radius: int = 0
     z_cosmo: float = 0.0
     flux_scale: float = 1.0
+    resample: int = 0
 
 
 # --------------------------------------------------------------------------

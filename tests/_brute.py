@@ -40,19 +40,41 @@ def projected(p):
             p.vy.astype(np.float64) * si + p.vz.astype(np.float64) * ci)
 
 
-def particle_spectrum(ssp, tel, mass, age, Z, v, spectra=None):
-    """m * T_interp(lambda_j / dop), T_interp bilinear in (log age, log Z), clamped,
-    and linear in wavelength with one zero node appended on either side."""
+def interpolated_template(ssp, age, Z, spectra=None):
+    """Template at (age, Z), bilinear in (log age, log Z) and clamped, with one
+    zero node appended on either side: (rest wavelengths, values)."""
     sp = ssp.spectra if spectra is None else spectra
     la = np.clip(math.log10(age), ssp.log10_age_nodes[0], ssp.log10_age_nodes[-1])
     lz = np.clip(math.log10(Z), ssp.log10_Z_nodes[0], ssp.log10_Z_nodes[-1])
     interp = RegularGridInterpolator((ssp.log10_age_nodes, ssp.log10_Z_nodes), sp, method="linear")
     T = interp([[la, lz]])[0]
     lam_s = ssp.lambda0 + ssp.dlambda * np.arange(-1, ssp.n_lambda + 1)
-    T_ext = np.concatenate([[0.0], T, [0.0]])
+    return lam_s, np.concatenate([[0.0], T, [0.0]])
+
+
+def particle_spectrum(ssp, tel, mass, age, Z, v, spectra=None):
+    """m * T_interp(lambda_j / dop), linear in wavelength (np.interp), or with
+    ``tel.resample`` = 1 the mean of that curve over each output bin."""
+    lam_s, T_ext = interpolated_template(ssp, age, Z, spectra)
+    dop = (1.0 + tel.z_cosmo) * (1.0 + v / C_KMS)
+    if getattr(tel, "resample", 0):
+        return tel.flux_scale * mass * bin_means(lam_s, T_ext, tel, dop)
     lam = tel.lambda0 + tel.dlambda * np.arange(tel.n_lambda)
-    lam_rest = lam / ((1.0 + tel.z_cosmo) * (1.0 + v / C_KMS))
-    return tel.flux_scale * mass * np.interp(lam_rest, lam_s, T_ext, left=0.0, right=0.0)
+    return tel.flux_scale * mass * np.interp(lam / dop, lam_s, T_ext, left=0.0, right=0.0)
+
+
+def bin_means(lam_s, T_ext, tel, dop):
+    """Mean of the piecewise-linear curve (lam_s, T_ext) over each output bin's
+    rest-frame interval: trapezoid rule with every curve node inside the
+    interval taken as a break point (exact for a piecewise-linear curve)."""
+    out = np.empty(tel.n_lambda)
+    for j in range(tel.n_lambda):
+        a = (tel.lambda0 + (j - 0.5) * tel.dlambda) / dop
+        b = (tel.lambda0 + (j + 0.5) * tel.dlambda) / dop
+        pts = np.concatenate([[a], lam_s[(lam_s > a) & (lam_s < b)], [b]])
+        vals = np.interp(pts, lam_s, T_ext, left=0.0, right=0.0)
+        out[j] = np.trapezoid(vals, pts) / (b - a)
+    return out
 
 
 def cube0(p, ssp, tel, spectra=None):

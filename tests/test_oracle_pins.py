@@ -215,6 +215,63 @@ def test_redshift_and_flux_scale_match_brute_force():
     assert np.abs(z0 - one).max() > 1e-3 * np.abs(one).max()
 
 
+# --------------------------------------------------------------------------
+# a5, flux-conserving alternative (reading R14): each output bin takes the
+# mean of the shifted spectrum over [lambda_j - dl/2, lambda_j + dl/2]
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dl", [0.7, 2.1, 5.3])
+def test_bin_mean_matches_brute_force(dl):
+    """Bins finer than, about equal to and coarser than the template spacing
+    (2 A): the oracle's segment sums against break-point trapezoids."""
+    ssp = tiny_ssp()
+    n_l = int(150 / dl)
+    tel = tiny_tel(psf_fwhm=0.0, lsf_sigma=0.0, dlambda=dl, n_lambda=n_l, lambda0=4003.0,
+                   z_cosmo=0.004, flux_scale=0.8, resample=1)
+    p = tiny_particles(n=30, vmax=900.0)
+    got = oracle.forward_parts(p, ssp, tel, n_threads=2)["cube0"]
+    bf = brute.cube0(p, ssp, tel)
+    np.testing.assert_allclose(got, bf, rtol=1e-11, atol=1e-11 * bf.max())
+    # the bin mean is not the centre sample
+    lin = oracle.forward_parts(p, ssp, tiny_tel(psf_fwhm=0.0, lsf_sigma=0.0, dlambda=dl, n_lambda=n_l,
+                                                lambda0=4003.0, z_cosmo=0.004, flux_scale=0.8),
+                               n_threads=2)["cube0"]
+    assert np.abs(lin - got).max() > 1e-4 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("dl", [0.9, 2.0, 3.7])
+def test_bin_mean_conserves_flux(dl):
+    """Closed form: with the output grid covering the shifted template's whole
+    support, sum_j S_j dl = fs m dop dls sum_k T[k] (each node's hat function
+    has unit area in node units), whatever the bin width and shift."""
+    ssp = tiny_ssp()
+    for v in (0.0, -310.0, 1234.5):
+        dop = 1.01 * (1.0 + float(np.float32(v)) / oracle.C_KMS)
+        lo = (ssp.lambda0 - 2 * ssp.dlambda) * dop - 3 * dl
+        hi = (ssp.lambda0 + (ssp.n_lambda + 1) * ssp.dlambda) * dop + 3 * dl
+        tel = tiny_tel(nx=1, ny=1, psf_fwhm=0.0, lsf_sigma=0.0, dlambda=dl, lambda0=lo,
+                       n_lambda=int((hi - lo) / dl) + 1, z_cosmo=0.01, flux_scale=1.7, resample=1)
+        p = _one(0.0, 0.0, 2.5e4, 0.8, 0.004, v)
+        row = oracle.forward_parts(p, ssp, tel, n_threads=1)["cube0"].reshape(-1)
+        _, T_ext = brute.interpolated_template(ssp, float(p.age[0]), float(p.Z[0]))
+        expect = 1.7 * float(p.mass[0]) * dop * ssp.dlambda * T_ext.sum()
+        assert abs(row.sum() * dl - expect) <= 1e-12 * expect
+
+
+def test_bin_mean_of_linear_template_is_centre_value():
+    """A template linear in wavelength: away from its ends the bin mean equals
+    the centre sample (the mean of a linear function over an interval is its
+    midpoint value), so resample = 1 and resample = 0 agree there."""
+    ssp = tiny_ssp()
+    lam = ssp.lambda0 + ssp.dlambda * np.arange(ssp.n_lambda)
+    slope = np.linspace(0.5, 2.0, ssp.n_age * ssp.n_Z).reshape(ssp.n_age, ssp.n_Z, 1)
+    ssp.spectra = (1.0 + slope * (lam - 4000.0) / 100.0) * np.ones((ssp.n_age, ssp.n_Z, 1))
+    kw = dict(nx=1, ny=1, psf_fwhm=0.0, lsf_sigma=0.0, lambda0=4020.0, dlambda=2.3, n_lambda=40)
+    p = _one(0.0, 0.0, 1.0e4, 2.2, 0.0011, 217.0)
+    a = oracle.forward_parts(p, ssp, tiny_tel(resample=1, **kw), n_threads=1)["cube0"].reshape(-1)
+    b = oracle.forward_parts(p, ssp, tiny_tel(**kw), n_threads=1)["cube0"].reshape(-1)
+    np.testing.assert_allclose(a, b, rtol=1e-12)
+
+
 def test_threads_do_not_change_values():
     ssp, tel = tiny_ssp(), tiny_tel()
     p = tiny_particles(n=200)
@@ -347,10 +404,10 @@ def _G0(G, tel):
     return oracle.psf(oracle.lsf(G, tel, 1), tel, 1)
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_gradient_matches_central_differences(seed):
+@pytest.mark.parametrize("seed,resample", [(0, 0), (1, 0), (2, 1), (3, 1)])
+def test_gradient_matches_central_differences(seed, resample):
     ssp = tiny_ssp()
-    tel = tiny_tel(nx=5, ny=4, n_lambda=48)
+    tel = tiny_tel(nx=5, ny=4, n_lambda=48, resample=resample)
     p = tiny_particles(n=25, seed=seed, spread=1.1)
     p.age = np.clip(p.age, 0.15, 12.0).astype(np.float32)   # stay inside the node range
     p.Z = np.clip(p.Z, 2e-4, 0.035).astype(np.float32)
