@@ -369,6 +369,25 @@ def run_extra(args, dev, flush):
         "grads_finite": ok}
     model.close()
     del d, cube, target
+    # mid-size workload with flux-conserving bin means (resample = 1)
+    tel_m = synth.Telescope(**{**wl.telescope.__dict__, "resample": 1})
+    model = CubeModel(wl.ssp, tel_m, "f32", max_particles=wl.particles.n, device=dev)
+    d = model.device_particles(wl.particles)
+    cube = torch.empty(model.cube_shape, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        model.forward(d, out=cube)
+    st = model.stats()
+    model.set_profiling(True)
+    t = _events_ms(torch, lambda: model.forward(d, out=cube), stream, max(3, min(args.steps, 10)), flush)
+    dep = model.profile_history("deposit")
+    model.set_profiling(False)
+    out["bin_means"] = {
+        "workload": "mid-disk-1e6p-150x150x3721-f32, resample = 1 (mean over each output bin)",
+        "ms_per_step": float(np.median(t)), "deposit_ms": float(np.median(dep)),
+        "deposits_per_s": st["deposits"] / (float(np.median(t)) / 1e3),
+        "slow_particle_tiles": st["slow_particle_tiles"]}
+    model.close()
+    del d, cube
     # large galaxy, BF16 templates
     wl = synth.large_galaxy()
     model = CubeModel(wl.ssp, wl.telescope, "bf16", max_particles=wl.particles.n, device=dev)

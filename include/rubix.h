@@ -92,6 +92,12 @@ typedef struct rubix_telescope {
     int32_t psf_radius, lsf_radius; /* kernel radii; <= 0 means ceil(4 sigma); each <= 64 */
     double z_cosmo;                 /* cosmological redshift of the galaxy (usually 0) */
     double flux_scale;              /* multiplies every spectrum (e.g. 1/(4 pi d_L^2)); 1 = none */
+    int32_t resample;               /* Sec. 3 "additional resampling" onto the output grid:
+                                     * 0 = the shifted template at each bin centre (linear
+                                     * interpolation between template nodes);
+                                     * 1 = its mean over each bin [lambda_j - dlambda/2,
+                                     * lambda_j + dlambda/2] (flux-conserving rebinning).
+                                     * rubix_cube_backward supports 0 only. */
 } rubix_telescope;
 
 /* Star particles (Sec. 3: input handler fields), float32 structure of arrays.

@@ -44,7 +44,8 @@ class rubix_telescope(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("spaxel_size", C.c_double),
                 ("n_lambda", C.c_int32), ("lambda0", C.c_double), ("dlambda", C.c_double),
                 ("psf_fwhm", C.c_double), ("lsf_sigma", C.c_double), ("psf_radius", C.c_int32),
-                ("lsf_radius", C.c_int32), ("z_cosmo", C.c_double), ("flux_scale", C.c_double)]
+                ("lsf_radius", C.c_int32), ("z_cosmo", C.c_double), ("flux_scale", C.c_double),
+                ("resample", C.c_int32)]
 
 
 class rubix_particles(C.Structure):

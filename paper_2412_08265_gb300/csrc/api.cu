@@ -251,6 +251,7 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     Plan& P = h->P;
     if (!P.have_forward) return fail(RUBIX_ERR_INVALID_ARG, "backward needs a forward on this handle first");
     if (P.forward_noise) return fail(RUBIX_ERR_INVALID_ARG, "backward of a noisy forward is not defined");
+    if (P.tel.resample) return fail(RUBIX_ERR_INVALID_ARG, "backward supports resample = 0 only");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(S.device));
     const float* G0 = dL_dcube;

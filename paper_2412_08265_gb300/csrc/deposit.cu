@@ -69,9 +69,11 @@ __global__ void k_setup(SetupParams P) {
         // t(j) = ((l0 + j dl) / dop - ls0) / dls = B + j A   (FP64)
         const double dop = (1.0 + P.z_cosmo) * (1.0 + v / kC_kms);
         const double alpha = 1.0 / (dop * P.ssp.dls);
-        const double B = P.l0 * alpha - P.ssp.ls0 / P.ssp.dls;
+        // bin means: the record maps j to bin j's lower edge, t(j) - A/2,
+        // and the edges run j = 0 .. n_lambda
         const double A = P.dl * alpha;
-        const double t_last = B + A * (double)(P.n_lambda - 1);
+        const double B = P.l0 * alpha - P.ssp.ls0 / P.ssp.dls - (P.resample ? 0.5 * A : 0.0);
+        const double t_last = B + A * (double)(P.resample ? P.n_lambda : P.n_lambda - 1);
         int bi = 0;
         float bf = 0.f, a_hi = 0.f, a_lo = 0.f;
         if (!(dop > 0.0) || !(B < (double)n_ls) || !(t_last >= -1.0) || !(B > -32768.0)) {
@@ -271,8 +273,9 @@ __device__ __forceinline__ void general_particle(const float4 w4, const float4 g
 // Fast-path setup of one particle for this tile and band: the slab offset of
 // its cell at node K0 (without the lane), frac(t(j0)) and 1 - dt/dj; false
 // if it takes the general path (dt/dj outside (1 - 1/31, 1], a cell of
-// another band, or a node of the rounds, K0 .. K0 + 31 R, outside the slab).
-template <int R>
+// another band, or a node of the rounds, K0 .. K0 + 31 R + EXTRA, outside the
+// slab).
+template <int R, int EXTRA = 0>
 __device__ __forceinline__ bool fast_setup(const float4 g4, const TileCtx& C, int& base, float& f, float& delta) {
     const int c0_bi = __float_as_int(g4.x);
     const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
@@ -281,7 +284,7 @@ __device__ __forceinline__ bool fast_setup(const float4 g4, const TileCtx& C, in
     const int kw = K0 - C.klo;
     const int cr = cell - C.cell0;
     base = kw * C.ncb + cr;
-    return delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R) &&
+    return delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R - EXTRA) &&
            (unsigned)cr < (unsigned)C.ncb;
 }
 
@@ -297,6 +300,128 @@ __device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g
         fast_rounds<R>(w4, slab + base + lane * C.ncb, f, delta, C.ncb, lane, lanef, acc);
     else
         general_particle<R>(w4, g4, C, slab, quad, lane, acc, slow_count);
+}
+
+// ----------------------------------------------------------------------------
+// Bin means (flux-conserving resampling). The record maps j to bin j's lower
+// edge e_j = t(j) - A/2 (node units); bin j's value is the mean of the
+// weighted template's linear interpolant M(t) over [e_j, e_{j+1}].
+//
+// Fast path (dt/dj = A = 1 - delta in (1 - 1/31, 1]): rounds of 30 bins.
+// Lane l of a round owns edge l, at node K0 + l + g with g = f - l delta in
+// (-1, 1), and bin l (l < 30) between edges l and l + 1. As in the centre
+// path, lane l reads node K0 + l's quad, forms M there and takes the
+// neighbouring node's M from lane l -+ 1, which gives the interpolant at its
+// edge, L_l. The interval of bin l holds at most one node,
+// K = K0 + l + (g >= 0), whose M is that neighbour's or the lane's own; with
+// a the distance from edge l to K and b = A - a, the trapezoids on both sides
+// of K give
+//   mean = M_K / 2 + (a L_l + b L_{l+1}) / (2A),
+// which also holds with no node inside (b < 0: the three points lie on one
+// line). L_{l+1} is one more shuffle. A tile of 31 R bins is R rounds of 30
+// bins and a last round of R bins, whose lanes above R + 1 read nothing: the
+// rounds read nodes K0 .. K0 + 31 R + 1.
+// ----------------------------------------------------------------------------
+template <int R>
+__device__ __forceinline__ void mean_rounds(const float4 w4, const float4* __restrict__ q, float f, float delta,
+                                            int ncb, int lane, float lanef, float (&acc)[R + 1]) {
+    const int s30 = 30 * ncb, s29 = 29 * ncb;
+    const float nld = -lanef * delta;
+    const float d30 = 30.f * delta;
+    const float A = 1.f - delta;
+    const float h = 0.5f / A;
+#pragma unroll
+    for (int r = 0; r <= R; ++r) {
+        float4 Q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < R || lane <= R + 1) Q = *q;
+        const float M = quad_dot(w4, Q);
+        const float g = f + nld;
+        const bool up = g >= 0.f;
+        const float X = __shfl_sync(0xffffffffu, M, up ? lane + 1 : lane - 1);
+        const float L = fmaf(fabsf(g), X - M, M);
+        const float Ln = __shfl_down_sync(0xffffffffu, L, 1);
+        const float MK = up ? X : M;
+        const float a = (up ? 1.f : 0.f) - g;
+        acc[r] += fmaf(0.5f, MK, h * fmaf(a, L, (A - a) * Ln));
+        if (r < R) {
+            // the next round starts at edge 30, 30 - 30 delta nodes further on
+            f -= d30;
+            const bool carry = f < 0.f;
+            f = carry ? f + 1.f : f;
+            q += carry ? s29 : s30;
+        }
+    }
+}
+
+// General path of the bin means: bin j (owned = a bin of this tile held by
+// this lane) integrates M segment by segment over [e_j, e_{j+1}], nodes from
+// the slab or, with use_slab false, from global memory.
+__device__ __noinline__ bool mean_in_slab(const float4 g4, const TileCtx C, int j, bool owned) {
+    if (!owned || j >= C.n_lambda) return true;
+    const int c0_bi = __float_as_int(g4.x);
+    if ((unsigned)(rec_c0(c0_bi) - C.cell0) >= (unsigned)C.ncb) return false;
+    float fa, fb;
+    const int ka = node_pos(j, rec_bi(c0_bi), g4.y, g4.z, g4.w, fa) - C.klo;
+    const int kb = node_pos(j + 1, rec_bi(c0_bi), g4.y, g4.z, g4.w, fb) - C.klo;
+    return ka >= 0 && kb + 1 < C.slab_w;
+}
+
+__device__ __noinline__ float mean_value(const float4 w4, const float4 g4, const TileCtx C, int j, bool owned,
+                                         bool use_slab, const float4* __restrict__ slab,
+                                         const float4* __restrict__ quad) {
+    if (!owned || j >= C.n_lambda) return 0.f;
+    const int c0_bi = __float_as_int(g4.x);
+    const int cell = rec_c0(c0_bi);
+    float fa, fb;
+    const int ka = node_pos(j, rec_bi(c0_bi), g4.y, g4.z, g4.w, fa);
+    const int kb = node_pos(j + 1, rec_bi(c0_bi), g4.y, g4.z, g4.w, fb);
+    auto node = [&](int k) {
+        const float4 q = use_slab ? slab[(k - C.klo) * C.ncb + (cell - C.cell0)]
+                                  : quad_global(quad, C.n_cells, C.n_ls, cell, k);
+        return quad_dot(w4, q);
+    };
+    // segments [k, k + 1] outside [-1, n_ls] are zero
+    const int k_first = max(ka, -1), k_last = min(kb, C.n_ls - 1);
+    float s = 0.f;
+    float m0 = node(k_first);
+    for (int k = k_first; k <= k_last; ++k) {
+        const float m1 = node(k + 1);
+        const float u0 = (k == ka) ? fa : 0.f, u1 = (k == kb) ? fb : 1.f;
+        s = fmaf(u1 - u0, fmaf(m1 - m0, 0.5f * (u0 + u1), m0), s);
+        m0 = m1;
+    }
+    const float len = (float)(kb - ka) + (fb - fa);
+    if (len > 0.f) return s / len;
+    const float ma = node(ka);  // a bin narrower than FP32 resolves: the edge value
+    return fmaf(fa, node(ka + 1) - ma, ma);
+}
+
+template <int R>
+__device__ __forceinline__ void mean_general_particle(const float4 w4, const float4 g4, const TileCtx& C,
+                                                      const float4* __restrict__ slab,
+                                                      const float4* __restrict__ quad, int lane,
+                                                      float (&acc)[R + 1], unsigned long long* slow_count) {
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i <= R; ++i) ok = ok && mean_in_slab(g4, C, C.j0 + 30 * i + lane, lane < (i < R ? 30 : R));
+    const bool use_slab = C.slab_w > 0 && __all_sync(0xffffffffu, ok);
+    if (!use_slab && lane == 0 && slow_count) atomicAdd(slow_count, 1ull);
+#pragma unroll
+    for (int i = 0; i <= R; ++i)
+        acc[i] += mean_value(w4, g4, C, C.j0 + 30 * i + lane, lane < (i < R ? 30 : R), use_slab, slab, quad);
+}
+
+template <int R>
+__device__ __forceinline__ void mean_particle(const float4 w4, const float4 g4, const TileCtx& C,
+                                              const float4* __restrict__ slab, const float4* __restrict__ quad,
+                                              int lane, float lanef, float (&acc)[R + 1],
+                                              unsigned long long* slow_count) {
+    int base;
+    float f, delta;
+    if (fast_setup<R, 1>(g4, C, base, f, delta))
+        mean_rounds<R>(w4, slab + base + lane * C.ncb, f, delta, C.ncb, lane, lanef, acc);
+    else
+        mean_general_particle<R>(w4, g4, C, slab, quad, lane, acc, slow_count);
 }
 
 // Per-tile cost of each job (in-field particles + cost_c0 per work item) and
@@ -321,7 +446,75 @@ constexpr int kJobChunk = 32;  // jobs per shared-memory work table
 #define RUBIX_DEP_RECPF 2
 #endif
 
-template <int R>
+// One work item's particles [q0, q1) of the current band, accumulated in
+// registers in sorted order, then stored (band 0) or added (later bands) to
+// the item's row dst. MEAN: bin means (rounds of 30 bins, R + 1 of them),
+// else centre samples (R rounds of 31).
+template <int R, bool MEAN>
+__device__ __forceinline__ void deposit_item(const DepositParams& P, const TileCtx& C, const float4* __restrict__ rec4,
+                                             int q0, int q1, float* dst, int band, const float4* __restrict__ slab,
+                                             int lane, float lanef) {
+    constexpr int NR = MEAN ? R + 1 : R;
+    float acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.f;
+#if !RUBIX_DEP_BANDADD
+    // later bands add to the row: start moving it into L2 now
+    if (band > 0 && lane < R && C.j0 + 31 * lane < P.n_lambda)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(dst + C.j0 + 31 * lane));
+#endif
+#if RUBIX_DEP_RECPF == 2
+    // the next particle's record is pulled into L1 while the current one is
+    // deposited (no registers held across the particle)
+    if (q0 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * q0));
+    for (int q = q0; q < q1; ++q) {
+        if (q + 1 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * (q + 1)));
+        const float4 w4 = rec4[2 * q], g4 = rec4[2 * q + 1];
+        if constexpr (MEAN)
+            mean_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
+        else
+            deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
+    }
+#else
+    // the next particle's record is in flight while the current one is deposited
+    float4 wn, gn;
+    if (q0 < q1) {
+        wn = rec4[2 * q0];
+        gn = rec4[2 * q0 + 1];
+    }
+    for (int q = q0; q < q1; ++q) {
+        const float4 w4 = wn, g4 = gn;
+        if (q + 1 < q1) {
+            wn = rec4[2 * (q + 1)];
+            gn = rec4[2 * (q + 1) + 1];
+        }
+        if constexpr (MEAN)
+            mean_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
+        else
+            deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
+    }
+#endif
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int j = MEAN ? C.j0 + 30 * r + lane : C.j0 + 31 * r + lane;
+        const bool owned = MEAN ? lane < (r < R ? 30 : R) : lane < 31;
+        if (owned && j < P.n_lambda) {
+            if (band == 0) {
+                dst[j] = acc[r];
+            } else {
+#if RUBIX_DEP_BANDADD
+                // one reduction per address and band, bands ordered by the
+                // CTA barrier: the sum order is fixed
+                atomicAdd(dst + j, acc[r]);
+#else
+                dst[j] += acc[r];
+#endif
+            }
+        }
+    }
+}
+
+template <int R, bool MEANS>
 __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_deposit(const __grid_constant__ DepositParams P,
                                                                    const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -456,56 +649,10 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_deposit(c
                     const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(J.rec);
                     float* dst = (pr < 0) ? J.cube + (long long)s * J.pitch
                                           : J.partials + (long long)pr * P.n_lambda;
-#if !RUBIX_DEP_BANDADD
-                    // later bands add to the row: start moving it into L2 now
-                    if (band > 0 && lane < R && C.j0 + 31 * lane < P.n_lambda)
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(dst + C.j0 + 31 * lane));
-#endif
-                    float acc[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r] = 0.f;
-#if RUBIX_DEP_RECPF == 2
-                    // the next particle's record is pulled into L1 while the current
-                    // one is deposited (no registers held across the particle)
-                    if (q0 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * q0));
-                    for (int q = q0; q < q1; ++q) {
-                        if (q + 1 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * (q + 1)));
-                        const float4 w4 = rec4[2 * q], g4 = rec4[2 * q + 1];
-                        deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
-                    }
-#else
-                    // the next particle's record is in flight while the current one is deposited
-                    float4 wn, gn;
-                    if (q0 < q1) {
-                        wn = rec4[2 * q0];
-                        gn = rec4[2 * q0 + 1];
-                    }
-                    for (int q = q0; q < q1; ++q) {
-                        const float4 w4 = wn, g4 = gn;
-                        if (q + 1 < q1) {
-                            wn = rec4[2 * (q + 1)];
-                            gn = rec4[2 * (q + 1) + 1];
-                        }
-                        deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
-                    }
-#endif
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const int j = C.j0 + 31 * r + lane;
-                        if (lane < 31 && j < P.n_lambda) {
-                            if (band == 0) {
-                                dst[j] = acc[r];
-                            } else {
-#if RUBIX_DEP_BANDADD
-                                // one reduction per address and band, bands ordered
-                                // by the CTA barrier: the sum order is fixed
-                                atomicAdd(dst + j, acc[r]);
-#else
-                                dst[j] += acc[r];
-#endif
-                            }
-                        }
-                    }
+                    if (MEANS && J.resample)
+                        deposit_item<R, true>(P, C, rec4, q0, q1, dst, band, slab, lane, lanef);
+                    else
+                        deposit_item<R, false>(P, C, rec4, q0, q1, dst, band, slab, lane, lanef);
                 }
             }
         }
@@ -516,10 +663,12 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_deposit(c
 int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,
                    cudaStream_t st) {
     if (P.tile_w % 31 != 0) return -1;
+    bool means = false;
+    for (int j = 0; j < P.n_jobs && j < kMaxJobs; ++j) means = means || P.jobs[j].resample;
     void (*fn)(const DepositParams, const CUtensorMap) = nullptr;
     switch (P.tile_w / 31) {
 #define RUBIX_DEP_R(r) \
-    case r: fn = k_deposit<r>; break;
+    case r: fn = means ? k_deposit<r, true> : k_deposit<r, false>; break;
         RUBIX_DEP_R(1) RUBIX_DEP_R(2) RUBIX_DEP_R(3) RUBIX_DEP_R(4) RUBIX_DEP_R(5) RUBIX_DEP_R(6)
         RUBIX_DEP_R(7) RUBIX_DEP_R(8) RUBIX_DEP_R(9) RUBIX_DEP_R(10) RUBIX_DEP_R(11) RUBIX_DEP_R(12)
 #if RUBIX_DEP_RMAX > 12

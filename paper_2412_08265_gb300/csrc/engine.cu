@@ -126,6 +126,7 @@ rubix_status validate_telescope(const rubix_telescope* tel, double ssp_dlambda) 
     if (!(tel->dlambda > 0.0)) return fail(RUBIX_ERR_INVALID_ARG, "dlambda must be > 0");
     if (!(tel->psf_fwhm >= 0.0) || !(tel->lsf_sigma >= 0.0)) return fail(RUBIX_ERR_INVALID_ARG, "negative PSF/LSF width");
     if (!(tel->z_cosmo > -1.0)) return fail(RUBIX_ERR_INVALID_ARG, "z_cosmo must be > -1");
+    if (tel->resample != 0 && tel->resample != 1) return fail(RUBIX_ERR_INVALID_ARG, "resample must be 0 or 1");
     if (tel->dlambda / ((1.0 + tel->z_cosmo) * ssp_dlambda) > 3.0)
         return fail(RUBIX_ERR_INVALID_ARG, "instrument bins wider than 3 SSP steps are not supported");
     const double sp = tel->psf_fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
@@ -649,6 +650,7 @@ rubix_status enqueue_pre(Plan& P, const rubix_particles* p, cudaStream_t st, cud
     SP.z_cosmo = P.tel.z_cosmo;
     SP.flux_scale = P.tel.flux_scale;
     SP.n_lambda = P.tel.n_lambda;
+    SP.resample = P.tel.resample;
     SP.rec = P.d_rec;
     SP.prec = P.d_prec;
     SP.n_cap = P.cap;
@@ -685,6 +687,7 @@ DepJob plan_job(const Plan& P, float* target) {
     J.part_cap = P.part_cap;
     J.n_s = P.n_s;
     J.pitch = (target == P.d_cube0) ? P.pitch0 : P.tel.n_lambda;
+    J.resample = P.tel.resample;
     return J;
 }
 

@@ -99,6 +99,7 @@ struct SetupParams {
     const double* v;         // line-of-sight velocity per particle
     double l0, dl, z_cosmo, flux_scale;
     int n_lambda;
+    int resample;            // 0: records map bin centres, 1: bin lower edges (bin means)
     DepRec* rec;             // [n_in]
     PartRec* prec;           // [n_in]
     long long n_cap;         // capacity of rec / prec
@@ -134,6 +135,7 @@ struct DepJob {
     long long part_cap;
     int n_s;
     int pitch;               // cube row stride in floats (>= n_lambda)
+    int resample;            // 1: bin means (records hold the bins' lower edges)
 };
 struct DepositParams {
     const float4* quad;      // [n_ls][n_cells] SSP cell quads (the four bilinear corners per node)

@@ -46,7 +46,8 @@ class CubeModel:
         return capi.rubix_telescope(int(tel.nx), int(tel.ny), float(tel.spaxel_size), int(tel.n_lambda),
                                     float(tel.lambda0), float(tel.dlambda), float(tel.psf_fwhm),
                                     float(tel.lsf_sigma), int(tel.psf_radius), int(tel.lsf_radius),
-                                    float(tel.z_cosmo), float(tel.flux_scale))
+                                    float(tel.z_cosmo), float(tel.flux_scale),
+                                    int(getattr(tel, "resample", 0)))
 
     @property
     def cube_shape(self):

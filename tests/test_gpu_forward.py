@@ -408,3 +408,64 @@ def test_forward_redshifted_and_scaled(torch_cuda, z):
     if z == 0.005:
         assert st["slow_particle_tiles"] == 0
     model.close()
+
+
+# ---------------------------------------------------------------------------
+# a5 flux-conserving alternative: bin means (resample = 1)
+@pytest.mark.parametrize("case", ["fast", "redshift_general", "coarse_bins", "fine_bins", "high_velocity"])
+def test_forward_bin_means(torch_cuda, case):
+    """Bin means against the oracle. "fast": dt/dj in (30/31, 1], every particle
+    on the 30-bin-round path; "redshift_general" (dt/dj < 30/31) and the coarse
+    (dt/dj ~ 2.3, several segments per bin) and fine (~0.65) grids take the
+    per-bin path; "high_velocity" mixes the global-memory path in."""
+    base = synth.mid_galaxy(n=40_000, seed=21)
+    p = base.particles
+    kw = dict(nx=20, ny=20, spaxel_size=0.5, n_lambda=3721, lambda0=4750.0, dlambda=1.25,
+              flux_scale=2e-3, resample=1)
+    if case == "redshift_general":
+        kw.update(z_cosmo=0.02)
+    elif case == "coarse_bins":
+        kw.update(n_lambda=1583, dlambda=2.9, lambda0=4760.0)
+    elif case == "fine_bins":
+        kw.update(n_lambda=1237, dlambda=0.8125, lambda0=4751.3)
+    elif case == "high_velocity":
+        p.v_los = p.v_los.copy()
+        p.v_los[::9] = np.float32(4000.0)
+        p.v_los[4::9] = np.float32(-3500.0)
+    tel = synth.Telescope(**kw)
+    model = make_model(base.ssp, tel, n=p.n)
+    got = model.forward(p).cpu().numpy()
+    ref = oracle.forward(p, base.ssp, tel, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_F32
+    st = model.stats()
+    assert st["device_error"] == 0
+    if case == "fast":
+        assert st["slow_particle_tiles"] == 0
+    if case == "high_velocity":
+        assert st["slow_particle_tiles"] > 0
+    # not the centre samples
+    lin = oracle.forward(p, base.ssp, synth.Telescope(**{**kw, "resample": 0}), n_threads=NT)
+    assert float(np.abs(lin - ref).max()) > 100 * TOL_F32 * float(np.abs(ref).max())
+    model.close()
+
+
+def test_bin_means_conserve_flux_and_reject_backward(torch_cuda):
+    """Flux: on a grid covering every shifted template, the pre-convolution
+    cube summed over wavelength times dlambda equals the oracle's (which equals
+    the templates' integrals, a closed form pinned on the CPU). Backward of a
+    bin-mean handle is refused with INVALID_ARG."""
+    from paper_2412_08265_gb300 import capi
+    ssp = synth.ssp_grid(6, 4, 600, 5000.0, 5600.0, seed=2)     # 1.0017 A steps
+    tel = synth.Telescope(nx=8, ny=8, spaxel_size=0.6, n_lambda=640, lambda0=4975.0, dlambda=1.0,
+                          psf_fwhm=0.0, lsf_sigma=0.0, resample=1)
+    p = synth.disk_projected(30_000, 4)
+    model = make_model(ssp, tel, n=p.n)
+    got = model.forward(p).cpu().numpy().astype(np.float64)
+    ref = oracle.forward(p, ssp, tel, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_F32
+    tot_g, tot_r = got.sum(axis=2), ref.sum(axis=2)
+    assert float(np.abs(tot_g - tot_r).max()) <= 1e-5 * float(tot_r.max())
+    with pytest.raises(capi.RubixError) as ei:
+        model.backward(torch_cuda.zeros(model.cube_shape, device="cuda"))
+    assert ei.value.status == capi.RUBIX_ERR_INVALID_ARG
+    model.close()

@@ -253,3 +253,26 @@ def test_concurrent_client_threads(env):
     srv.close()
     for a, o in zip(alone, outs):
         assert np.array_equal(a.view(np.uint32), o.cpu().numpy().view(np.uint32))
+
+
+def test_bin_means_share_launches_with_centre_samples(env):
+    """Requests with resample = 1 (bin means) and 0 (centre samples) in shared
+    deposit launches: every cube equals the same request served alone,
+    bitwise, and a served bin-mean request matches the oracle."""
+    torch, ssp = env
+    reqs = [(p, synth.Telescope(**{**tel.__dict__, "resample": i % 2}))
+            for i, (p, tel) in enumerate(requests(10, seed=41, n_hi=8e4, side_hi=40))]
+    srv = server(ssp, slots=1, batch=1)
+    alone = [run_all(torch, srv, [r])[0][0] for r in reqs]
+    srv.close()
+    srv = server(ssp, slots=10, batch=10)
+    mix, _ = run_all(torch, srv, reqs)
+    st = srv.stats()
+    assert st["ok"] == len(reqs) and st["max_batch"] > 1
+    srv.close()
+    for i, (a, b) in enumerate(zip(alone, mix)):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), i
+    for i in (1, 3):
+        p, tel = reqs[i]
+        ref = oracle.forward(p, ssp, tel, n_threads=NT)
+        assert float(np.abs(mix[i].astype(np.float64) - ref).max() / np.abs(ref).max()) <= TOL_F32
