@@ -96,8 +96,7 @@ typedef struct rubix_telescope {
                                      * 0 = the shifted template at each bin centre (linear
                                      * interpolation between template nodes);
                                      * 1 = its mean over each bin [lambda_j - dlambda/2,
-                                     * lambda_j + dlambda/2] (flux-conserving rebinning).
-                                     * rubix_cube_backward supports 0 only. */
+                                     * lambda_j + dlambda/2] (flux-conserving rebinning). */
 } rubix_telescope;
 
 /* Star particles (Sec. 3: input handler fields), float32 structure of arrays.

@@ -200,7 +200,160 @@ __device__ __forceinline__ AdjSums adj_particle(const float4 w, const float4 g4,
     return S;
 }
 
+// ---------------------------------------------------------------------------
+// Bin means (resample = 1). With S_j the mean of the weighted interpolant over
+// [e_j, e_{j+1}] (node units, width A) and the edges moving with v as
+// t' = -(t + ls0/dls) / (c (1 + v/c)), differentiating the bounds gives
+//   dS_j/dv = -1/(c (1 + v/c)) [ (L_{j+1} u_{j+1} - L_j u_j) / A - S_j ]
+//           = -1/(c (1 + v/c)) [ u_j (L_{j+1} - L_j) / A + L_{j+1} - S_j ],
+// L_j the interpolant at edge j and u_j = e_j + ls0/dls (u_{j+1} = u_j + A);
+// sv sums G_j times the bracket, and sm, sa, sz sum G_j times the bin means
+// of the three weighted interpolants (M, and the a- and b-weighted forms).
+// ---------------------------------------------------------------------------
+__device__ __noinline__ AdjSums adj_mean_bin(const float4 w, const float4 wa, const float4 wb, const float4 g4,
+                                             const TileCtx C, int j, float Gj, bool use_slab, const float4* slab,
+                                             const float4* quad, float ls0_over) {
+    AdjSums S{0.f, 0.f, 0.f, 0.f};
+    const int c0_bi = __float_as_int(g4.x);
+    const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
+    float fa, fb;
+    const int ka = node_pos(j, bi, g4.y, g4.z, g4.w, fa);
+    const int kb = node_pos(j + 1, bi, g4.y, g4.z, g4.w, fb);
+    auto node = [&](int k) {
+        return use_slab ? slab[(k - C.klo) * C.ncb + (cell - C.cell0)] : quad_global(quad, C.n_cells, C.n_ls, cell, k);
+    };
+    const float len = (float)(kb - ka) + (fb - fa);
+    if (!(len > 0.f)) return S;
+    const int k_first = max(ka, -1), k_last = min(kb, C.n_ls - 1);
+    float im = 0.f, ia = 0.f, ib = 0.f;
+    float4 q0 = node(k_first);
+    float m0 = quad_dot(w, q0), a0 = quad_dot(wa, q0), b0 = quad_dot(wb, q0);
+    for (int k = k_first; k <= k_last; ++k) {
+        const float4 q1 = node(k + 1);
+        const float m1 = quad_dot(w, q1), a1 = quad_dot(wa, q1), b1 = quad_dot(wb, q1);
+        const float u0 = (k == ka) ? fa : 0.f, u1 = (k == kb) ? fb : 1.f;
+        const float d = u1 - u0, mid = 0.5f * (u0 + u1);
+        im = fmaf(d, fmaf(m1 - m0, mid, m0), im);
+        ia = fmaf(d, fmaf(a1 - a0, mid, a0), ia);
+        ib = fmaf(d, fmaf(b1 - b0, mid, b0), ib);
+        m0 = m1;
+        a0 = a1;
+        b0 = b1;
+    }
+    const float inv = 1.f / len;
+    const float4 qa0 = node(ka), qa1 = node(ka + 1), qb0 = node(kb), qb1 = node(kb + 1);
+    const float ma = quad_dot(w, qa0), mb = quad_dot(w, qb0);
+    const float La = fmaf(fa, quad_dot(w, qa1) - ma, ma), Lb = fmaf(fb, quad_dot(w, qb1) - mb, mb);
+    const float Sm = im * inv;
+    S.sm = Gj * Sm;
+    S.sa = Gj * (ia * inv);
+    S.sz = Gj * (ib * inv);
+    const float u = ((float)ka + fa) + ls0_over;
+    S.sv = Gj * fmaf(u * (Lb - La), inv, Lb - Sm);
+    return S;
+}
+
+// General path of the bin means: bin j0 + 30 r + l on lane l (l < 30; the
+// last round holds R bins), nodes from the slab when every bin of the warp
+// has its nodes there, else from global memory.
 template <int R>
+__device__ __noinline__ AdjSums adj_mean_general(const float4 w, const float4 g4, const TileCtx C, const float4* slab,
+                                                 const float4* quad, int lane, const float (&G)[R + 1],
+                                                 float ls0_over) {
+    const int c0_bi = __float_as_int(g4.x);
+    const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
+    bool ok = C.slab_w > 0 && (unsigned)(cell - C.cell0) < (unsigned)C.ncb;
+#pragma unroll
+    for (int r = 0; r <= R; ++r) {
+        const int j = C.j0 + 30 * r + lane;
+        if (lane < (r < R ? 30 : R) && j < C.n_lambda) {
+            float fa, fb;
+            const int ka = node_pos(j, bi, g4.y, g4.z, g4.w, fa) - C.klo;
+            const int kb = node_pos(j + 1, bi, g4.y, g4.z, g4.w, fb) - C.klo;
+            ok = ok && ka >= 0 && kb + 1 < C.slab_w;
+        }
+    }
+    const bool use_slab = __all_sync(0xffffffffu, ok);
+    const float s01 = w.x + w.y, s23 = w.z + w.w, s02 = w.x + w.z, s13 = w.y + w.w;
+    const float4 wa = make_float4(-s01, s01, -s23, s23), wb = make_float4(-s02, -s13, s02, s13);
+    AdjSums S{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r <= R; ++r) {
+        const int j = C.j0 + 30 * r + lane;
+        if (!(lane < (r < R ? 30 : R) && j < C.n_lambda)) continue;
+        const AdjSums b = adj_mean_bin(w, wa, wb, g4, C, j, G[r], use_slab, slab, quad, ls0_over);
+        S.sm += b.sm;
+        S.sa += b.sa;
+        S.sz += b.sz;
+        S.sv += b.sv;
+    }
+    return S;
+}
+
+// Fast path of the bin means: the forward's 30-bin rounds (edge l on lane l;
+// see mean_rounds in deposit.cu) for the three interpolants at once.
+template <int R>
+__device__ __forceinline__ AdjSums adj_mean_particle(const float4 w, const float4 g4, const TileCtx& C,
+                                                     const float4* __restrict__ slab,
+                                                     const float4* __restrict__ quad, int lane, float lanef,
+                                                     const float (&G)[R + 1], float ls0_over) {
+    const int c0_bi = __float_as_int(g4.x);
+    const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
+    float f;
+    const int K0 = node_pos(C.j0, bi, g4.y, g4.z, g4.w, f);
+    const float delta = (1.f - g4.z) - g4.w;
+    const int kw = K0 - C.klo;
+    const int cr = cell - C.cell0;
+    if (!(delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R - 1) &&
+          (unsigned)cr < (unsigned)C.ncb))
+        return adj_mean_general<R>(w, g4, C, slab, quad, lane, G, ls0_over);
+    const float s01 = w.x + w.y, s23 = w.z + w.w, s02 = w.x + w.z, s13 = w.y + w.w;
+    const float4 wa = make_float4(-s01, s01, -s23, s23), wb = make_float4(-s02, -s13, s02, s13);
+    const float4* q = slab + (kw + lane) * C.ncb + cr;
+    const int s30 = 30 * C.ncb, s29 = 29 * C.ncb;
+    const float nld = -lanef * delta;
+    const float d30 = 30.f * delta;
+    const float A = 1.f - delta;
+    const float h = 0.5f / A, iA = 1.f / A;
+    float tb = ((float)K0 + lanef) + ls0_over;  // absolute node position of lane l's node, / dls
+    AdjSums S{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r <= R; ++r) {
+        float4 Q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < R || lane <= R + 1) Q = *q;
+        const float M = quad_dot(w, Q), Ma = quad_dot(wa, Q), Mb = quad_dot(wb, Q);
+        const float g = f + nld;
+        const bool up = g >= 0.f;
+        const int src = up ? lane + 1 : lane - 1;
+        const float XM = __shfl_sync(0xffffffffu, M, src);
+        const float XA = __shfl_sync(0xffffffffu, Ma, src);
+        const float XB = __shfl_sync(0xffffffffu, Mb, src);
+        const float ag = fabsf(g);
+        const float LM = fmaf(ag, XM - M, M), LA = fmaf(ag, XA - Ma, Ma), LB = fmaf(ag, XB - Mb, Mb);
+        const float LMn = __shfl_down_sync(0xffffffffu, LM, 1);
+        const float LAn = __shfl_down_sync(0xffffffffu, LA, 1);
+        const float LBn = __shfl_down_sync(0xffffffffu, LB, 1);
+        const float a = (up ? 1.f : 0.f) - g, b = A - a;
+        const float Sm = fmaf(0.5f, up ? XM : M, h * fmaf(a, LM, b * LMn));
+        const float Sa = fmaf(0.5f, up ? XA : Ma, h * fmaf(a, LA, b * LAn));
+        const float Sb = fmaf(0.5f, up ? XB : Mb, h * fmaf(a, LB, b * LBn));
+        const float Gj = G[r];  // 0 for lanes that own no bin of the tile
+        S.sm = fmaf(Gj, Sm, S.sm);
+        S.sa = fmaf(Gj, Sa, S.sa);
+        S.sz = fmaf(Gj, Sb, S.sz);
+        S.sv = fmaf(Gj, fmaf((tb + g) * (LMn - LM), iA, LMn - Sm), S.sv);
+        if (r < R) {
+            f -= d30;
+            const bool carry = f < 0.f;
+            f = carry ? f + 1.f : f;
+            q += carry ? s29 : s30;
+            tb += carry ? 29.f : 30.f;
+        }
+    }
+    return S;
+}
+
+template <int R, bool MEAN>
 __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_tiles(const __grid_constant__ AdjTileParams P,
                                                                          const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -300,20 +453,27 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
                     const int q1 = __shfl_sync(0xffffffffu, qe, src);
                     const int s = __shfl_sync(0xffffffffu, sp, src);
                     // this tile's slice of the spaxel's dL/dcube0 row, one bin per lane and round
-                    float G[R];
+                    constexpr int NR = MEAN ? R + 1 : R;
+                    float G[NR];
                     const float* __restrict__ grow = P.G0 + (long long)s * P.n_lambda;
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const int j = C.j0 + 31 * r + lane;
-                        G[r] = (lane < 31 && j < P.n_lambda) ? grow[j] : 0.f;
+                    for (int r = 0; r < NR; ++r) {
+                        const int j = MEAN ? C.j0 + 30 * r + lane : C.j0 + 31 * r + lane;
+                        const bool owned = MEAN ? lane < (r < R ? 30 : R) : lane < 31;
+                        G[r] = (owned && j < P.n_lambda) ? grow[j] : 0.f;
                     }
                     for (int q = q0; q < q1; ++q) {
                         if (q + 1 < q1) {
                             asm volatile("prefetch.global.L1 [%0];" ::"l"(P.wu + q + 1));
                             asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * (q + 1) + 1));
                         }
-                        AdjSums S = adj_particle<R>(P.wu[q], rec4[2 * q + 1], C, slab, P.quad, lane, lanef, G,
-                                                    P.ls0_over);
+                        AdjSums S;
+                        if constexpr (MEAN)
+                            S = adj_mean_particle<R>(P.wu[q], rec4[2 * q + 1], C, slab, P.quad, lane, lanef, G,
+                                                     P.ls0_over);
+                        else
+                            S = adj_particle<R>(P.wu[q], rec4[2 * q + 1], C, slab, P.quad, lane, lanef, G,
+                                                P.ls0_over);
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) {
                             S.sm += __shfl_xor_sync(0xffffffffu, S.sm, o);
@@ -335,7 +495,7 @@ int launch_adjoint_tiles(const AdjTileParams& P, const CUtensorMap* tmap, int n_
     void (*fn)(const AdjTileParams, const CUtensorMap) = nullptr;
     switch (P.tile_w / 31) {
 #define RUBIX_ADJ_R(r) \
-    case r: fn = k_adjoint_tiles<r>; break;
+    case r: fn = P.resample ? k_adjoint_tiles<r, true> : k_adjoint_tiles<r, false>; break;
         RUBIX_ADJ_R(1) RUBIX_ADJ_R(2) RUBIX_ADJ_R(3) RUBIX_ADJ_R(4) RUBIX_ADJ_R(5) RUBIX_ADJ_R(6)
         RUBIX_ADJ_R(7) RUBIX_ADJ_R(8) RUBIX_ADJ_R(9) RUBIX_ADJ_R(10) RUBIX_ADJ_R(11) RUBIX_ADJ_R(12)
 #if RUBIX_DEP_RMAX > 12

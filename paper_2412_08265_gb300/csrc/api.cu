@@ -251,7 +251,6 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     Plan& P = h->P;
     if (!P.have_forward) return fail(RUBIX_ERR_INVALID_ARG, "backward needs a forward on this handle first");
     if (P.forward_noise) return fail(RUBIX_ERR_INVALID_ARG, "backward of a noisy forward is not defined");
-    if (P.tel.resample) return fail(RUBIX_ERR_INVALID_ARG, "backward supports resample = 0 only");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(S.device));
     const float* G0 = dL_dcube;
@@ -285,6 +284,7 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     A.contrib = d_global ? P.d_contrib : nullptr;
     A.n_in = P.last_n;  // upper bound; the kernel reads the in-field count on the device
 #ifdef RUBIX_ADJ_WARP
+    if (P.tel.resample) return fail(RUBIX_ERR_INVALID_ARG, "this build's backward supports resample = 0 only");
     launch_adjoint_rec(A, P.d_rec, st);  // one warp per particle over every bin
 #else
     // over the deposit's (tile, work item, age band) decomposition and slabs
@@ -314,6 +314,7 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     T.n_boxes = S.n_boxes;
     T.cost_c0 = S.cost_c0;
     T.ls0_over = (float)(S.ssp.ls0 / S.ssp.dls);
+    T.resample = P.tel.resample;
     T.err = S.d_err;
     if (launch_adjoint_tiles(T, &S.tmap, S.dep_ctas, S.dep_threads, S.dep_smem, st) < 0)
         return fail(RUBIX_ERR_CUDA, "adjoint launch failed: %s", cudaGetErrorString(cudaGetLastError()));

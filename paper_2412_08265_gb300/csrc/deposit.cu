@@ -325,24 +325,74 @@ __device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g
 template <int R>
 __device__ __forceinline__ void mean_rounds(const float4 w4, const float4* __restrict__ q, float f, float delta,
                                             int ncb, int lane, float lanef, float (&acc)[R + 1]) {
+    // with the weights halved (M' = M/2, L' = L/2), and a L + b L_{l+1} =
+    // a (L - L_{l+1}) + A L_{l+1}, the mean is M'_K + L'_{l+1} + (a/A)(L' - L'_{l+1})
+    const float4 wh = make_float4(0.5f * w4.x, 0.5f * w4.y, 0.5f * w4.z, 0.5f * w4.w);
     const int s30 = 30 * ncb, s29 = 29 * ncb;
     const float nld = -lanef * delta;
     const float d30 = 30.f * delta;
-    const float A = 1.f - delta;
-    const float h = 0.5f / A;
+    const float iA = 1.f / (1.f - delta);
+    const int lp = lane + 1, lm = lane - 1;
+#if RUBIX_DEP_PAIR2
+    // rounds two at a time: the per-bin arithmetic in packed FP32x2
+#pragma unroll
+    for (int r = 0; r + 1 <= R; r += 2) {
+        float4 Qa = *q;
+        const float fa = f;
+        f -= d30;
+        bool carry = f < 0.f;
+        f = carry ? f + 1.f : f;
+        q += carry ? s29 : s30;
+        float4 Qb = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r + 1 < R || lane <= R + 1) Qb = *q;
+        const float fb = f;
+        if (r + 2 <= R) {
+            f -= d30;
+            carry = f < 0.f;
+            f = carry ? f + 1.f : f;
+            q += carry ? s29 : s30;
+        }
+        const float2 M = make_float2(quad_dot(wh, Qa), quad_dot(wh, Qb));
+        const float2 g = __fadd2_rn(make_float2(fa, fb), make_float2(nld, nld));
+        const bool ua = g.x >= 0.f, ub = g.y >= 0.f;
+        const float2 X = make_float2(__shfl_sync(0xffffffffu, M.x, ua ? lp : lm),
+                                     __shfl_sync(0xffffffffu, M.y, ub ? lp : lm));
+        const float2 L = __ffma2_rn(make_float2(fabsf(g.x), fabsf(g.y)), __fadd2_rn(X, make_float2(-M.x, -M.y)), M);
+        const float2 Ln = make_float2(__shfl_down_sync(0xffffffffu, L.x, 1), __shfl_down_sync(0xffffffffu, L.y, 1));
+        const float2 MK = make_float2(ua ? X.x : M.x, ub ? X.y : M.y);
+        const float2 ai = __ffma2_rn(make_float2(-g.x, -g.y), make_float2(iA, iA),
+                                     make_float2(ua ? iA : 0.f, ub ? iA : 0.f));
+        const float2 v = __ffma2_rn(ai, __fadd2_rn(L, make_float2(-Ln.x, -Ln.y)), __fadd2_rn(MK, Ln));
+        const float2 a = __fadd2_rn(make_float2(acc[r], acc[r + 1]), v);
+        acc[r] = a.x;
+        acc[r + 1] = a.y;
+    }
+    if (!(R & 1)) {
+        // R + 1 rounds, odd: the last round (R bins) alone
+        float4 Q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane <= R + 1) Q = *q;
+        const float M = quad_dot(wh, Q);
+        const float g = f + nld;
+        const bool up = g >= 0.f;
+        const float X = __shfl_sync(0xffffffffu, M, up ? lp : lm);
+        const float L = fmaf(fabsf(g), X - M, M);
+        const float Ln = __shfl_down_sync(0xffffffffu, L, 1);
+        const float ai = fmaf(-g, iA, up ? iA : 0.f);
+        acc[R] += fmaf(ai, L - Ln, (up ? X : M) + Ln);
+    }
+#else
 #pragma unroll
     for (int r = 0; r <= R; ++r) {
         float4 Q = make_float4(0.f, 0.f, 0.f, 0.f);
         if (r < R || lane <= R + 1) Q = *q;
-        const float M = quad_dot(w4, Q);
+        const float M = quad_dot(wh, Q);
         const float g = f + nld;
         const bool up = g >= 0.f;
-        const float X = __shfl_sync(0xffffffffu, M, up ? lane + 1 : lane - 1);
+        const float X = __shfl_sync(0xffffffffu, M, up ? lp : lm);
         const float L = fmaf(fabsf(g), X - M, M);
         const float Ln = __shfl_down_sync(0xffffffffu, L, 1);
-        const float MK = up ? X : M;
-        const float a = (up ? 1.f : 0.f) - g;
-        acc[r] += fmaf(0.5f, MK, h * fmaf(a, L, (A - a) * Ln));
+        const float ai = fmaf(-g, iA, up ? iA : 0.f);  // a / A
+        acc[r] += fmaf(ai, L - Ln, (up ? X : M) + Ln);
         if (r < R) {
             // the next round starts at edge 30, 30 - 30 delta nodes further on
             f -= d30;
@@ -351,6 +401,7 @@ __device__ __forceinline__ void mean_rounds(const float4 w4, const float4* __res
             q += carry ? s29 : s30;
         }
     }
+#endif
 }
 
 // General path of the bin means: bin j (owned = a bin of this tile held by

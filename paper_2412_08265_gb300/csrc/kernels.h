@@ -225,6 +225,7 @@ struct AdjTileParams {
     int slab_w, ncb, box_w, n_boxes;
     int cost_c0;
     float ls0_over;             // ls0 / dls: node index -> rest wavelength / dls
+    int resample;               // 1: bin means (records hold the bins' lower edges)
     unsigned* err;
 };
 int launch_adjoint_tiles(const AdjTileParams& P, const CUtensorMap* tmap, int n_ctas, int threads, size_t smem,

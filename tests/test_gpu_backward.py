@@ -131,3 +131,27 @@ def test_backward_redshifted_and_scaled(torch_cuda, z):
     rng = np.random.default_rng(11)
     G = rng.standard_normal((tel.ny, tel.nx, tel.n_lambda))
     _grad_check(torch_cuda, wl, G)
+
+
+@pytest.mark.parametrize("case", ["fast", "redshift_general", "coarse_bins", "high_velocity"])
+def test_backward_bin_means(torch_cuda, case):
+    """Adjoint of the bin means (resample = 1) against the oracle's gradient,
+    which differentiates the bin edges too; the cases take the 30-bin-round
+    fast path, the per-bin path (dt/dj < 30/31 or ~2.3) and the global path."""
+    base = synth.mid_galaxy(n=30_000, seed=12)
+    p = base.particles
+    kw = dict(nx=20, ny=20, spaxel_size=0.5, n_lambda=3721, lambda0=4750.0, dlambda=1.25,
+              flux_scale=4e-3, resample=1)
+    if case == "redshift_general":
+        kw.update(z_cosmo=0.02)
+    elif case == "coarse_bins":
+        kw.update(n_lambda=1583, dlambda=2.9, lambda0=4760.0)
+    elif case == "high_velocity":
+        p.v_los = p.v_los.copy()
+        p.v_los[::9] = np.float32(4000.0)
+        p.v_los[4::9] = np.float32(-3500.0)
+    tel = synth.Telescope(**kw)
+    wl = synth.Workload("mid-bin-means", p, base.ssp, tel)
+    rng = np.random.default_rng(13)
+    G = rng.standard_normal((tel.ny, tel.nx, tel.n_lambda))
+    _grad_check(torch_cuda, wl, G)

@@ -449,12 +449,10 @@ def test_forward_bin_means(torch_cuda, case):
     model.close()
 
 
-def test_bin_means_conserve_flux_and_reject_backward(torch_cuda):
+def test_bin_means_conserve_flux(torch_cuda):
     """Flux: on a grid covering every shifted template, the pre-convolution
     cube summed over wavelength times dlambda equals the oracle's (which equals
-    the templates' integrals, a closed form pinned on the CPU). Backward of a
-    bin-mean handle is refused with INVALID_ARG."""
-    from paper_2412_08265_gb300 import capi
+    the templates' integrals, a closed form pinned on the CPU)."""
     ssp = synth.ssp_grid(6, 4, 600, 5000.0, 5600.0, seed=2)     # 1.0017 A steps
     tel = synth.Telescope(nx=8, ny=8, spaxel_size=0.6, n_lambda=640, lambda0=4975.0, dlambda=1.0,
                           psf_fwhm=0.0, lsf_sigma=0.0, resample=1)
@@ -465,7 +463,4 @@ def test_bin_means_conserve_flux_and_reject_backward(torch_cuda):
     assert rel_err(got, ref) <= TOL_F32
     tot_g, tot_r = got.sum(axis=2), ref.sum(axis=2)
     assert float(np.abs(tot_g - tot_r).max()) <= 1e-5 * float(tot_r.max())
-    with pytest.raises(capi.RubixError) as ei:
-        model.backward(torch_cuda.zeros(model.cube_shape, device="cuda"))
-    assert ei.value.status == capi.RUBIX_ERR_INVALID_ARG
     model.close()
