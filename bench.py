@@ -486,8 +486,38 @@ def run_ours(args):
         for _ in range(k_e2e):
             capi.rubix_cube_forward(model.handle, cp, 0, 0.0, hcube.data_ptr(), 0, stream.cuda_stream)
         t_e2e = (time.perf_counter() - t0) / k_e2e
-        e2e = {"value": deposits / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e}
+        single = {"value": deposits / t_e2e, "ms_per_step": 1e3 * t_e2e,
+                  "api": "rubix_cube_forward, host buffers, one call at a time (the call returns after the copy)"}
+        # the same galaxy as a stream of requests through the server
+        # (rubix_serve_submit), host inputs and host cubes, a few requests in
+        # flight so that one request's copies overlap another's kernels
+        from paper_2412_08265_gb300.serve import Server
+        depth = 3
+        srv = Server(wl.ssp, wl.telescope, hbm_budget_bytes=16 << 30, max_slots=depth, max_batch=1, device=dev)
+        outs = [torch.empty(model.cube_shape, dtype=torch.float32).pin_memory() for _ in range(depth)]
+        din = {**host, "preprojected": True, "inclination": 0.0}
+
+        def burst(k):
+            tks = []
+            for i in range(k):
+                if i >= depth and srv.wait(tks[i - depth], 60.0) != 0:
+                    raise RuntimeError("served request failed: " + capi.last_error_message())
+                tks.append(srv.submit(wl.telescope, din, outs[i % depth]))
+            for t in tks[max(0, k - depth):]:
+                if srv.wait(t, 60.0) != 0:
+                    raise RuntimeError("served request failed: " + capi.last_error_message())
+
+        burst(2 * depth)
+        k_srv = max(3 * depth, min(args.steps, 10) * 2)
+        t0 = time.perf_counter()
+        burst(k_srv)
+        t_srv = (time.perf_counter() - t0) / k_srv
+        srv.close()
+        e2e = {"value": deposits / t_srv, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_srv,
+               "api": f"rubix_serve_submit, host buffers (page-locked), {depth} requests in flight, "
+                      f"{k_srv} requests timed",
+               "single_call": single}
 
     if rank != 0:
         if ws > 1:

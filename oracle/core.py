@@ -55,18 +55,24 @@ def _nthreads(n_threads):
     return max(1, int(n_threads))
 
 
-def orient(p):
-    """a1: projected positions (x', y') and line-of-sight velocity, FP64."""
+def orient(p, derivatives=False):
+    """a1: projected positions (x', y') and line-of-sight velocity, FP64; with
+    ``derivatives`` also dv_los/d(inclination) and dv_los/d(azimuth)."""
     lib = _load()
     n = p.n
     xp = np.empty(n); yp = np.empty(n); v = np.empty(n)
-    ci, si = math.cos(p.inclination), math.sin(p.inclination)
+    di = np.empty(n) if derivatives else None
+    da = np.empty(n) if derivatives else None
     f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
     lib.or_orient(C.c_int64(n), _p(f32(p.x), np.float32), _p(f32(p.y), np.float32),
-                  _p(f32(p.z), np.float32), _p(f32(p.vy), np.float32), _p(f32(p.vz), np.float32),
+                  _p(f32(p.z), np.float32), _p(f32(getattr(p, "vx", None)), np.float32),
+                  _p(f32(p.vy), np.float32), _p(f32(p.vz), np.float32),
                   _p(f32(p.v_los), np.float32), C.c_int(1 if p.preprojected else 0),
-                  C.c_double(ci), C.c_double(si), _p(xp, np.float64), _p(yp, np.float64),
-                  _p(v, np.float64))
+                  C.c_double(p.inclination), C.c_double(getattr(p, "azimuth", 0.0)),
+                  C.c_double(getattr(p, "position_angle", 0.0)), _p(xp, np.float64),
+                  _p(yp, np.float64), _p(v, np.float64), _p(di, np.float64), _p(da, np.float64))
+    if derivatives:
+        return xp, yp, v, di, da
     return xp, yp, v
 
 

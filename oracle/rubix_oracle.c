@@ -31,31 +31,63 @@
 #define OR_C_KMS 299792.458 /* speed of light, km/s */
 
 /* ---------------------------------------------------------------------- */
-/* a1: orientation (Sec. 3: the galaxy is rotated into the field of view). */
-/* Reading: rotation about the x axis by the inclination i; the line of    */
-/* sight is the rotated z axis.                                            */
-/*   x' = x,  y' = y cos i - z sin i,  v_los = vy sin i + vz cos i.        */
-/* Each product and the difference/sum is rounded once (FP64, no FMA).     */
-/* cos i and sin i are passed in (computed once on the host).              */
+/* a1: orientation (Sec. 3: the galaxy is rotated into the field of view   */
+/* as its configuration says). Reading: three rotations of the galaxy      */
+/* frame, first by the azimuth a about its own z axis, then by the         */
+/* inclination i about x, then by the position angle q about the line of   */
+/* sight z:  R = Rz(q) Rx(i) Rz(a),  Rz(t) = [[c,-s,0],[s,c,0],[0,0,1]],    */
+/* Rx(t) = [[1,0,0],[0,c,-s],[0,s,c]].  x' = (R r)_x, y' = (R r)_y,         */
+/* v_los = (R v)_z. With ca = cos a, sa = sin a, ci, si, cq, sq likewise:  */
+/*   R00 = cq ca - sq (ci sa)     R01 = -(cq sa) - sq (ci ca)   R02 = sq si */
+/*   R10 = sq ca + cq (ci sa)     R11 = cq (ci ca) - sq sa      R12 = -(cq si) */
+/*   R20 = si sa                  R21 = si ca                   R22 = ci    */
+/* each product and sum rounded once in FP64 in the order written, and     */
+/*   x' = (R00 x + R01 y) + R02 z   (likewise y', v_los), no FMA.           */
+/* With a = q = 0 this is x' = x, y' = y cos i - z sin i,                  */
+/* v_los = vy sin i + vz cos i. The derivatives of v_los that the global   */
+/* gradients need (positions have none, reading R12):                      */
+/*   dv/di = (ci sa) vx + (ci ca) vy - si vz,  dv/da = si (ca vx - sa vy). */
+/* vx may be NULL when a = 0 (its coefficients are then zero).             */
 /* ---------------------------------------------------------------------- */
-int or_orient(int64_t n, const float *x, const float *y, const float *z,
-              const float *vy, const float *vz, const float *vlos, int preprojected,
-              double cos_i, double sin_i, double *xp, double *yp, double *v)
+static void or_rotation(double incl, double azim, double pa, double R[9])
 {
+    double ca = cos(azim), sa = sin(azim), ci = cos(incl), si = sin(incl);
+    double cq = cos(pa), sq = sin(pa);
+    R[0] = cq * ca - sq * (ci * sa);
+    R[1] = -(cq * sa) - sq * (ci * ca);
+    R[2] = sq * si;
+    R[3] = sq * ca + cq * (ci * sa);
+    R[4] = cq * (ci * ca) - sq * sa;
+    R[5] = -(cq * si);
+    R[6] = si * sa;
+    R[7] = si * ca;
+    R[8] = ci;
+}
+
+int or_orient(int64_t n, const float *x, const float *y, const float *z, const float *vx,
+              const float *vy, const float *vz, const float *vlos, int preprojected,
+              double incl, double azim, double pa, double *xp, double *yp, double *v,
+              double *dv_di, double *dv_da)
+{
+    double R[9];
+    or_rotation(incl, azim, pa, R);
+    double ca = cos(azim), sa = sin(azim), ci = cos(incl), si = sin(incl);
     for (int64_t p = 0; p < n; ++p) {
         if (preprojected) {
             xp[p] = (double)x[p];
             yp[p] = (double)y[p];
             v[p] = (double)vlos[p];
-        } else {
-            double a = (double)y[p] * cos_i;
-            double b = (double)z[p] * sin_i;
-            double c = (double)vy[p] * sin_i;
-            double d = (double)vz[p] * cos_i;
-            xp[p] = (double)x[p];
-            yp[p] = a - b;
-            v[p] = c + d;
+            if (dv_di) dv_di[p] = 0.0;
+            if (dv_da) dv_da[p] = 0.0;
+            continue;
         }
+        double X = (double)x[p], Y = (double)y[p], Z = (double)z[p];
+        double VX = vx ? (double)vx[p] : 0.0, VY = (double)vy[p], VZ = (double)vz[p];
+        xp[p] = (R[0] * X + R[1] * Y) + R[2] * Z;
+        yp[p] = (R[3] * X + R[4] * Y) + R[5] * Z;
+        v[p] = (R[6] * VX + R[7] * VY) + R[8] * VZ;
+        if (dv_di) dv_di[p] = ((ci * sa) * VX + (ci * ca) * VY) - si * VZ;
+        if (dv_da) dv_da[p] = si * (ca * VX - sa * VY);
     }
     return 0;
 }

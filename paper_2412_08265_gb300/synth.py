@@ -42,7 +42,9 @@ class Particles:
     When ``preprojected`` is True, ``x``/``y`` are sky-plane coordinates in kpc
     and ``v_los`` is the line-of-sight velocity in km/s; ``z``/``vx``/``vy``/
     ``vz`` are unused. Otherwise ``x, y, z`` and ``vx, vy, vz`` are 3-D and the
-    galaxy is inclined by ``inclination`` (radians) about the x axis.
+    galaxy frame is turned by ``azimuth`` about its own z axis, inclined by
+    ``inclination`` about x and turned by ``position_angle`` about the line of
+    sight (radians; R = Rz(position_angle) Rx(inclination) Rz(azimuth)).
     """
 
     x: np.ndarray
@@ -57,6 +59,8 @@ class Particles:
     vz: np.ndarray | None = None
     preprojected: bool = True
     inclination: float = 0.0
+    azimuth: float = 0.0
+    position_angle: float = 0.0
 
     @property
     def n(self) -> int:
@@ -69,7 +73,8 @@ class Particles:
                          age=take(self.age), Z=take(self.Z), v_los=take(self.v_los),
                          z=take(self.z), vx=take(self.vx), vy=take(self.vy),
                          vz=take(self.vz), preprojected=self.preprojected,
-                         inclination=self.inclination)
+                         inclination=self.inclination, azimuth=self.azimuth,
+                         position_angle=self.position_angle)
 
 
 @dataclass
@@ -183,7 +188,7 @@ def bulge_plus_disk_projected(n: int, seed: int, bulge_frac: float = 0.3,
 
 def disk_3d(n: int, seed: int, inclination: float, r_scale: float = 3.0,
             h_scale: float = 0.3, v_circ: float = 200.0, r_turn: float = 2.0,
-            sigma_v: float = 50.0) -> Particles:
+            sigma_v: float = 50.0, azimuth: float = 0.0, position_angle: float = 0.0) -> Particles:
     """3-D rotating exponential disk in the x-y plane, to be inclined by the library."""
     rng = np.random.Generator(np.random.PCG64(seed))
     R = rng.gamma(2.0, r_scale, n)
@@ -197,7 +202,8 @@ def disk_3d(n: int, seed: int, inclination: float, r_scale: float = 3.0,
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     return Particles(x=f32(R * np.cos(phi)), y=f32(R * np.sin(phi)), z=f32(zz),
                      vx=f32(vx), vy=f32(vy), vz=f32(vz), mass=mass, age=age, Z=Z,
-                     preprojected=False, inclination=float(inclination))
+                     preprojected=False, inclination=float(inclination), azimuth=float(azimuth),
+                     position_angle=float(position_angle))
 
 
 # --------------------------------------------------------------------------

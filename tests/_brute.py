@@ -31,13 +31,24 @@ def exact_spaxel(xp: float, yp: float, tel):
     return None
 
 
+def rotation(p):
+    """Rotation matrix of the orientation: scipy's extrinsic z-x-z Euler
+    rotation (azimuth about z, then inclination about x, then the position
+    angle about z)."""
+    from scipy.spatial.transform import Rotation
+    return Rotation.from_euler("zxz", [getattr(p, "azimuth", 0.0), p.inclination,
+                                       getattr(p, "position_angle", 0.0)]).as_matrix()
+
+
 def projected(p):
     if p.preprojected:
         return (p.x.astype(np.float64), p.y.astype(np.float64), p.v_los.astype(np.float64))
-    ci, si = math.cos(p.inclination), math.sin(p.inclination)
-    y = p.y.astype(np.float64); z = p.z.astype(np.float64)
-    return (p.x.astype(np.float64), y * ci - z * si,
-            p.vy.astype(np.float64) * si + p.vz.astype(np.float64) * ci)
+    R = rotation(p)
+    r = np.stack([p.x, p.y, p.z]).astype(np.float64)
+    vx = np.zeros(p.n) if p.vx is None else p.vx.astype(np.float64)
+    vel = np.stack([vx, p.vy.astype(np.float64), p.vz.astype(np.float64)])
+    rp, vp = R @ r, R @ vel
+    return rp[0], rp[1], vp[2]
 
 
 def interpolated_template(ssp, age, Z, spectra=None):

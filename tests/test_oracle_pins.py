@@ -65,6 +65,63 @@ def test_orientation_is_a_rotation():
     np.testing.assert_allclose(yp * yp + z_rot * z_rot, y * y + z * z, rtol=1e-12, atol=1e-14)
 
 
+def test_orientation_euler_angles_match_scipy():
+    """R = Rz(position angle) Rx(inclination) Rz(azimuth) against scipy's
+    extrinsic z-x-z Euler rotation, for random angles."""
+    rng = np.random.default_rng(4)
+    for k in range(6):
+        p = synth.disk_3d(200, 40 + k, inclination=float(rng.uniform(0, math.pi)),
+                          azimuth=float(rng.uniform(-math.pi, math.pi)),
+                          position_angle=float(rng.uniform(-math.pi, math.pi)))
+        got = oracle.orient(p)
+        ref = brute.projected(p)
+        for a, b in zip(got, ref):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * np.abs(b).max())
+
+
+def test_orientation_inclination_only_is_bitwise_the_plain_formula():
+    """Azimuth and position angle 0: x' = x, y' = y cos i - z sin i and
+    v_los = vy sin i + vz cos i, each operation rounded once (bitwise)."""
+    p = synth.disk_3d(1000, 13, inclination=0.83)
+    xp, yp, v = oracle.orient(p)
+    ci, si = math.cos(0.83), math.sin(0.83)
+    f = lambda a: a.astype(np.float64)
+    assert np.array_equal(xp, f(p.x))
+    assert np.array_equal(yp, f(p.y) * ci - f(p.z) * si)
+    assert np.array_equal(v, f(p.vy) * si + f(p.vz) * ci)
+
+
+def test_position_angle_turns_the_sky_plane():
+    """The position angle rotates (x', y') about the line of sight and leaves
+    v_los bitwise unchanged."""
+    p = synth.disk_3d(500, 14, inclination=0.6, azimuth=0.3)
+    x0, y0, v0 = oracle.orient(p)
+    q = 1.1
+    p.position_angle = q
+    x1, y1, v1 = oracle.orient(p)
+    assert np.array_equal(v0, v1)
+    np.testing.assert_allclose(x1, math.cos(q) * x0 - math.sin(q) * y0, atol=1e-12)
+    np.testing.assert_allclose(y1, math.sin(q) * x0 + math.cos(q) * y0, atol=1e-12)
+
+
+def test_orientation_velocity_derivatives():
+    """dv_los/d(inclination) and dv_los/d(azimuth) against central differences."""
+    p = synth.disk_3d(300, 15, inclination=0.9, azimuth=-0.4, position_angle=0.2)
+    _, _, v, di, da = oracle.orient(p, derivatives=True)
+    h = 1e-6
+    for name, d in (("inclination", di), ("azimuth", da)):
+        x0 = getattr(p, name)
+        setattr(p, name, x0 + h)
+        vp = oracle.orient(p)[2]
+        setattr(p, name, x0 - h)
+        vm = oracle.orient(p)[2]
+        setattr(p, name, x0)
+        np.testing.assert_allclose(d, (vp - vm) / (2 * h), rtol=0, atol=1e-6 * np.abs(d).max())
+    pp = tiny_particles(n=10)
+    _, _, _, di, da = oracle.orient(pp, derivatives=True)
+    assert not di.any() and not da.any()
+
+
 # --------------------------------------------------------------------------
 # a2 spaxel keys (reading C1/C3: half-open spaxels, FoV centred on 0)
 # --------------------------------------------------------------------------
@@ -442,6 +499,40 @@ def test_gradient_matches_central_differences(seed, resample):
             assert abs(fd - grad[i]) <= 2e-4 * scale + 1e-9 * abs(L0), (name, i, fd, grad[i])
             checked += 1
     assert checked >= 40
+
+
+@pytest.mark.parametrize("resample", [0, 1])
+def test_orientation_gradients_match_central_differences(resample):
+    """Gradients of the shared orientation angles, dL/d(angle) =
+    sum_p dL/dv_p dv_p/d(angle) (positions carry none, R12), against central
+    differences of the FP64 loss, with a step that moves no particle to
+    another spaxel."""
+    ssp = tiny_ssp()
+    tel = tiny_tel(nx=5, ny=4, n_lambda=48, resample=resample)
+    p = synth.disk_3d(30, 17, inclination=0.7, azimuth=0.5, position_angle=0.3, r_scale=0.8)
+    p.age = np.clip(p.age, 0.15, 12.0).astype(np.float32)
+    p.Z = np.clip(p.Z, 2e-4, 0.035).astype(np.float32)
+    rng = np.random.default_rng(23)
+    target = oracle.forward(p, ssp, tel, 1) * (1 + 0.2 * rng.standard_normal((tel.ny, tel.nx, tel.n_lambda)))
+    L0, G = _loss_and_G(p, ssp, tel, target)
+    parts = oracle.forward_parts(p, ssp, tel, 1)
+    assert (parts["key"] < tel.nx * tel.ny).sum() >= 10
+    _, _, _, dv = oracle.gradient(parts["key"], parts["v"], p, ssp, tel, _G0(G, tel), 1)
+    _, _, _, di, da = oracle.orient(p, derivatives=True)
+    h = 1e-6
+    for name, dd in (("inclination", di), ("azimuth", da)):
+        pred = float((dv * dd).sum())
+        x0 = getattr(p, name)
+        Ls = []
+        for x in (x0 + h, x0 - h):
+            setattr(p, name, x)
+            key = oracle.spaxel_keys(*oracle.orient(p)[:2], tel)
+            assert np.array_equal(key, parts["key"])
+            Ls.append(_loss_and_G(p, ssp, tel, target)[0])
+        setattr(p, name, x0)
+        fd = (Ls[0] - Ls[1]) / (2 * h)
+        assert abs(fd - pred) <= 1e-5 * max(abs(fd), abs(pred)) + 1e-9 * abs(L0), (name, fd, pred)
+        assert abs(pred) > 1e-6 * abs(L0)
 
 
 def test_mass_gradient_closed_form():
