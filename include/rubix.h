@@ -13,9 +13,16 @@
  *
  * Readings of the steps the paper leaves unspecified (all implemented exactly
  * this way by the library):
- *   - Orientation: rotation about the x axis by the inclination i:
- *       x' = x, y' = y cos i - z sin i, v_los = vy sin i + vz cos i
- *     (FP64, each product and sum rounded once; cos i, sin i from the host).
+ *   - Orientation: the galaxy frame is turned by the azimuth a about its own
+ *     z axis, inclined by i about x, then turned by the position angle q about
+ *     the line of sight: R = Rz(q) Rx(i) Rz(a), with (c = cos, s = sin, host
+ *     libm, FP64, each product and sum rounded once in the order written)
+ *       R00 = cq ca - sq (ci sa)   R01 = -(cq sa) - sq (ci ca)   R02 = sq si
+ *       R10 = sq ca + cq (ci sa)   R11 = cq (ci ca) - sq sa      R12 = -(cq si)
+ *       R20 = si sa                R21 = si ca                   R22 = ci
+ *     x' = (R00 x + R01 y) + R02 z, y' likewise, v_los = (R20 vx + R21 vy) + R22 vz,
+ *     no FMA. With a = q = 0: x' = x, y' = y cos i - z sin i,
+ *     v_los = vy sin i + vz cos i.
  *   - Spaxels: nx*ny squares of side spaxel_size centred on (0, 0), half-open;
  *     x_lo = (-0.5*nx)*size, u = (x' - x_lo) * (1/size) in FP64, ix = floor(u).
  *     Particles outside the field are dropped.
@@ -23,6 +30,9 @@
  *   - Doppler + resampling: rest wavelength of output bin j is
  *     (lambda0 + j*dlambda) / ((1 + z_cosmo)(1 + v_los/c)); the template is
  *     linearly interpolated there, and is zero outside its wavelength range.
+ *     With rubix_telescope.resample = 1 the bin takes instead the mean of that
+ *     interpolant over the bin [lambda_j - dlambda/2, lambda_j + dlambda/2]
+ *     mapped to the rest frame (flux-conserving rebinning).
  *   - Spectrum of a particle = flux_scale * mass * interpolated template.
  *   - PSF: 2-D Gaussian, sigma = FWHM / (2 sqrt(2 ln 2)) spaxels; LSF: 1-D
  *     Gaussian, sigma = lsf_sigma / dlambda bins; both sampled at integer
@@ -103,7 +113,9 @@ typedef struct rubix_telescope {
  * preprojected = 1: x, y are sky-plane positions (kpc) and v_los (km/s) is
  *                   given; z, vx, vy, vz are ignored (may be NULL).
  * preprojected = 0: x, y, z (kpc) and vx, vy, vz (km/s) are 3-D; the galaxy
- *                   is inclined by `inclination` radians about the x axis.
+ *                   is oriented by `azimuth`, `inclination` and
+ *                   `position_angle` (radians, see Orientation above); vx may
+ *                   be NULL when azimuth = 0.
  * mass: Msun; age: Gyr (> 0); Z: metal mass fraction (> 0).
  * on_device = 1: all pointers are device pointers; 0: host pointers (copied
  * to the device inside the call; pinned memory makes the copy asynchronous). */
@@ -114,6 +126,7 @@ typedef struct rubix_particles {
     int32_t on_device;
     int32_t preprojected;
     double inclination;
+    double azimuth, position_angle;
 } rubix_particles;
 
 typedef struct rubix_cube rubix_cube_t;
@@ -144,9 +157,13 @@ rubix_status rubix_cube_forward(rubix_cube_t *h, const rubix_particles *p, uint6
  * [ny][nx][n_lambda]. Outputs (device pointers, float32 [n], original particle
  * order, any may be NULL): dL/dmass, dL/dage (per Gyr), dL/dZ, dL/dv_los
  * (per km/s). Out-of-field particles get 0. d_global (device, nullable,
- * float64[2]): [0] = dL/dv_sys (a systemic velocity added to every particle)
- * = sum of dL/dv_los; [1] = dL/dln(M) for a global mass scale = sum of
- * mass * dL/dmass, both summed in FP64 in a fixed order.
+ * float64[4]), gradients of parameters every particle shares: [0] = dL/dv_sys
+ * (a systemic velocity added to every particle) = sum of dL/dv_los; [1] =
+ * dL/dln(M) for a global mass scale = sum of mass * dL/dmass; [2] =
+ * dL/d(inclination) = sum of dL/dv_los * dv_los/di; [3] = dL/d(azimuth)
+ * likewise (positions carry no gradient, so the position angle has none and
+ * preprojected input gives 0 for [2] and [3]); each summed in FP64 in a fixed
+ * order.
  * Errors: INVALID_ARG (no forward yet, or the forward used noise), CUDA. */
 rubix_status rubix_cube_backward(rubix_cube_t *h, const float *dL_dcube, float *d_mass,
                                  float *d_age, float *d_Z, float *d_vlos, double *d_global,

@@ -52,7 +52,8 @@ class rubix_particles(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p), ("v_los", C.c_void_p),
                 ("mass", C.c_void_p), ("age", C.c_void_p), ("Z", C.c_void_p),
-                ("on_device", C.c_int32), ("preprojected", C.c_int32), ("inclination", C.c_double)]
+                ("on_device", C.c_int32), ("preprojected", C.c_int32), ("inclination", C.c_double),
+                ("azimuth", C.c_double), ("position_angle", C.c_double)]
 
 
 class RubixError(RuntimeError):

@@ -104,8 +104,11 @@ __global__ void __launch_bounds__(256) k_adjoint(const AdjointParams P, const De
             if (P.d_Z) P.d_Z[p] = dZ;
             if (P.d_v) P.d_v[p] = dv;
             if (P.contrib) {
-                P.contrib[2 * i] = (double)dv;
-                P.contrib[2 * i + 1] = (double)pr.mass * (double)dm;
+                const float2 da = P.dv_dang ? P.dv_dang[p] : make_float2(0.f, 0.f);
+                P.contrib[kGlobal * i] = (double)dv;
+                P.contrib[kGlobal * i + 1] = (double)pr.mass * (double)dm;
+                P.contrib[kGlobal * i + 2] = (double)dv * (double)da.x;
+                P.contrib[kGlobal * i + 3] = (double)dv * (double)da.y;
             }
         }
     }
@@ -144,50 +147,48 @@ int launch_zero_grads(float* a, float* b, float* c, float* d, long long n, cudaS
     return 1;
 }
 
-// K8: fixed-order FP64 reduction of contrib[n][2] -> out[2].
+// K8: fixed-order FP64 reduction of contrib[n][kGlobal] -> out[kGlobal]
+// (each block sums a contiguous range, then one thread adds the blocks in order).
 constexpr int kRedBlocks = 256;
 __global__ void __launch_bounds__(256) k_reduce_partial(const double* __restrict__ contrib, const int* __restrict__ n_dev,
                                                         double* __restrict__ part) {
-    __shared__ double s0[256], s1[256];
+    __shared__ double sh[kGlobal][256];
     const long long n = *n_dev;
     const long long per = (n + gridDim.x - 1) / gridDim.x;
     const long long b = per * blockIdx.x, e = min(b + per, n);
-    double a0 = 0.0, a1 = 0.0;
-    for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
-        a0 += contrib[2 * i];
-        a1 += contrib[2 * i + 1];
-    }
-    s0[threadIdx.x] = a0;
-    s1[threadIdx.x] = a1;
+    double a[kGlobal];
+#pragma unroll
+    for (int c = 0; c < kGlobal; ++c) a[c] = 0.0;
+    for (long long i = b + threadIdx.x; i < e; i += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < kGlobal; ++c) a[c] += contrib[kGlobal * i + c];
+#pragma unroll
+    for (int c = 0; c < kGlobal; ++c) sh[c][threadIdx.x] = a[c];
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            s0[threadIdx.x] += s0[threadIdx.x + o];
-            s1[threadIdx.x] += s1[threadIdx.x + o];
-        }
+        if (threadIdx.x < o)
+#pragma unroll
+            for (int c = 0; c < kGlobal; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = s0[0];
-        part[2 * blockIdx.x + 1] = s1[0];
-    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c < kGlobal; ++c) part[kGlobal * blockIdx.x + c] = sh[c][0];
 }
 
 __global__ void k_reduce_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double a0 = 0.0, a1 = 0.0;
-        for (int i = 0; i < nb; ++i) {
-            a0 += part[2 * i];
-            a1 += part[2 * i + 1];
-        }
-        out[0] = a0;
-        out[1] = a1;
+        double a[kGlobal];
+        for (int c = 0; c < kGlobal; ++c) a[c] = 0.0;
+        for (int i = 0; i < nb; ++i)
+            for (int c = 0; c < kGlobal; ++c) a[c] += part[kGlobal * i + c];
+        for (int c = 0; c < kGlobal; ++c) out[c] = a[c];
     }
 }
 
-int launch_reduce_global(const double* contrib, const int* n_in_dev, double* out2, double* scratch, cudaStream_t st) {
+int launch_reduce_global(const double* contrib, const int* n_in_dev, double* out, double* scratch, cudaStream_t st) {
     k_reduce_partial<<<kRedBlocks, 256, 0, st>>>(contrib, n_in_dev, scratch);
-    k_reduce_final<<<1, 32, 0, st>>>(scratch, kRedBlocks, out2);
+    k_reduce_final<<<1, 32, 0, st>>>(scratch, kRedBlocks, out);
     return 2;
 }
 

@@ -544,8 +544,11 @@ __global__ void k_adj_final(const AdjointParams P, const float4* __restrict__ pa
         if (P.d_Z) P.d_Z[p] = dZ;
         if (P.d_v) P.d_v[p] = dv;
         if (P.contrib) {
-            P.contrib[2 * i] = (double)dv;
-            P.contrib[2 * i + 1] = (double)pr.mass * (double)dm;
+            const float2 da = P.dv_dang ? P.dv_dang[p] : make_float2(0.f, 0.f);
+            P.contrib[kGlobal * i] = (double)dv;
+            P.contrib[kGlobal * i + 1] = (double)pr.mass * (double)dm;
+            P.contrib[kGlobal * i + 2] = (double)dv * (double)da.x;
+            P.contrib[kGlobal * i + 3] = (double)dv * (double)da.y;
         }
     }
 }

@@ -282,6 +282,7 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     A.d_Z = d_Z;
     A.d_v = d_vlos;
     A.contrib = d_global ? P.d_contrib : nullptr;
+    A.dv_dang = P.d_dvda;
     A.n_in = P.last_n;  // upper bound; the kernel reads the in-field count on the device
 #ifdef RUBIX_ADJ_WARP
     if (P.tel.resample) return fail(RUBIX_ERR_INVALID_ARG, "this build's backward supports resample = 0 only");

@@ -146,8 +146,31 @@ rubix_status check_particles(const rubix_particles* p) {
         if (!p->v_los) return fail(RUBIX_ERR_INVALID_ARG, "v_los required when preprojected");
     } else {
         if (!p->z || !p->vy || !p->vz) return fail(RUBIX_ERR_INVALID_ARG, "z, vy, vz required when not preprojected");
+        if (!p->vx && p->azimuth != 0.0) return fail(RUBIX_ERR_INVALID_ARG, "vx required when azimuth != 0");
     }
     return RUBIX_OK;
+}
+
+void orientation_matrix(double inclination, double azimuth, double position_angle, double R[9], double Di[3],
+                        double Da[2]) {
+    const double ca = std::cos(azimuth), sa = std::sin(azimuth);
+    const double ci = std::cos(inclination), si = std::sin(inclination);
+    const double cq = std::cos(position_angle), sq = std::sin(position_angle);
+    const double cisa = ci * sa, cica = ci * ca;
+    R[0] = cq * ca - sq * cisa;
+    R[1] = -(cq * sa) - sq * cica;
+    R[2] = sq * si;
+    R[3] = sq * ca + cq * cisa;
+    R[4] = cq * cica - sq * sa;
+    R[5] = -(cq * si);
+    R[6] = si * sa;
+    R[7] = si * ca;
+    R[8] = ci;
+    Di[0] = cisa;
+    Di[1] = cica;
+    Di[2] = -si;
+    Da[0] = si * ca;
+    Da[1] = -(si * sa);
 }
 
 bool same_wavelength_grid(const SspState& S, const rubix_telescope* tel) {
@@ -377,7 +400,8 @@ std::vector<Buf> plan_buffers(Plan* P, const SspState& S, int n_s, int n_lambda,
     std::vector<Buf> v;
     if (staging)
         v = {{(void**)&P->d_x, 4 * N},    {(void**)&P->d_y, 4 * N},    {(void**)&P->d_z, 4 * N},
-             {(void**)&P->d_vy, 4 * N},   {(void**)&P->d_vz, 4 * N},   {(void**)&P->d_vlos, 4 * N},
+             {(void**)&P->d_vx, 4 * N},   {(void**)&P->d_vy, 4 * N},   {(void**)&P->d_vz, 4 * N},
+             {(void**)&P->d_vlos, 4 * N},
              {(void**)&P->d_mass, 4 * N}, {(void**)&P->d_age, 4 * N}, {(void**)&P->d_Z, 4 * N}};
     const std::vector<Buf> rest = {
         {(void**)&P->d_key, 4 * N},
@@ -398,7 +422,8 @@ std::vector<Buf> plan_buffers(Plan* P, const SspState& S, int n_s, int n_lambda,
     if (need_tmp || with_grad) v.push_back({(void**)&P->d_tmp, cube});
     if (with_out) v.push_back({(void**)&P->d_out, cube});
     if (with_grad) {
-        v.push_back({(void**)&P->d_contrib, 16 * N});
+        v.push_back({(void**)&P->d_contrib, 8 * kGlobal * N});
+        v.push_back({(void**)&P->d_dvda, 8 * N});
         v.push_back({(void**)&P->d_red, 8 * 1024});
         v.push_back({(void**)&P->d_wu, 16 * N});
         v.push_back({(void**)&P->d_adjpart, 16 * N * (size_t)std::max(S.n_tiles, 1)});
@@ -556,19 +581,20 @@ namespace {
 rubix_status stage_particles(Plan& P, const rubix_particles* p, const float** arrs, cudaStream_t st) {
     const long long n = p->n;
     const float* src[10] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->v_los, p->mass, p->age, p->Z};
-    float* dst[10] = {P.d_x, P.d_y, P.d_z, nullptr, P.d_vy, P.d_vz, P.d_vlos, P.d_mass, P.d_age, P.d_Z};
+    float* dst[10] = {P.d_x, P.d_y, P.d_z, P.d_vx, P.d_vy, P.d_vz, P.d_vlos, P.d_mass, P.d_age, P.d_Z};
     for (int i = 0; i < 10; ++i) {
         arrs[i] = nullptr;
         if (!src[i] || n == 0) continue;
         if (p->on_device) {
             arrs[i] = src[i];
-        } else if (i != 3) {
+        } else if (!p->preprojected || i < 2 || i > 5) {
+            // host arrays the call reads (the 3-D ones only for 3-D input)
             if (!dst[i]) return fail(RUBIX_ERR_INVALID_ARG, "host particle arrays need a plan with staging buffers");
             CK(cudaMemcpyAsync(dst[i], src[i], (size_t)n * 4, cudaMemcpyHostToDevice, st));
             arrs[i] = dst[i];
         }
     }
-    if (p->preprojected) arrs[2] = arrs[4] = arrs[5] = nullptr;
+    if (p->preprojected) arrs[2] = arrs[3] = arrs[4] = arrs[5] = nullptr;
     else arrs[6] = nullptr;
     return RUBIX_OK;
 }
@@ -579,12 +605,12 @@ AssignParams assign_params(const Plan& P, const rubix_particles* p, const float*
     A.x = arrs[0];
     A.y = arrs[1];
     A.z = arrs[2];
+    A.vx = arrs[3];
     A.vy = arrs[4];
     A.vz = arrs[5];
     A.v_los = arrs[6];
     A.preprojected = p->preprojected ? 1 : 0;
-    A.cos_i = std::cos(p->inclination);
-    A.sin_i = std::sin(p->inclination);
+    orientation_matrix(p->inclination, p->azimuth, p->position_angle, A.R, A.Di, A.Da);
     A.x_lo = P.x_lo;
     A.y_lo = P.y_lo;
     A.inv_size = P.inv_size;
@@ -623,6 +649,7 @@ rubix_status enqueue_pre(Plan& P, const rubix_particles* p, cudaStream_t st, cud
         AssignParams A = assign_params(P, p, arrs);
         A.key = P.d_key;
         A.v_out = P.d_v;
+        A.dv_dang = P.d_dvda;  // null unless the plan keeps backward state
         A.age = arrs[8];
         A.la_nodes = S.d_la;
         A.n_age = S.ssp.n_age;

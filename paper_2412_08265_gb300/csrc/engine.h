@@ -52,6 +52,11 @@ void ssp_state_destroy(SspState* S);
 bool same_wavelength_grid(const SspState& S, const rubix_telescope* tel);
 // Particle descriptor checks shared by every entry point (arrays present, n in range).
 rubix_status check_particles(const rubix_particles* p);
+// Orientation R = Rz(position_angle) Rx(inclination) Rz(azimuth), row-major,
+// each element rounded as the header's reading states, and the coefficients
+// of dv_los/d(inclination) (Di, on vx, vy, vz) and dv_los/d(azimuth) (Da, on vx, vy).
+void orientation_matrix(double inclination, double azimuth, double position_angle, double R[9], double Di[3],
+                        double Da[2]);
 
 // Where a plan's device buffers come from: cudaMalloc, or stream-ordered
 // allocation on `stream` from `pool` (the server, which must not synchronise).
@@ -74,7 +79,8 @@ struct Plan {
     ConvParams conv{};
     bool need_conv = false;
     long long cap = 0, item_cap = 0, part_cap = 0;
-    float *d_x = nullptr, *d_y = nullptr, *d_z = nullptr, *d_vy = nullptr, *d_vz = nullptr, *d_vlos = nullptr;
+    float *d_x = nullptr, *d_y = nullptr, *d_z = nullptr, *d_vx = nullptr, *d_vy = nullptr, *d_vz = nullptr,
+          *d_vlos = nullptr;
     float *d_mass = nullptr, *d_age = nullptr, *d_Z = nullptr;
     int *d_key = nullptr, *d_keys_tmp = nullptr, *d_vals_tmp = nullptr, *d_skeys = nullptr, *d_perm = nullptr;
     double* d_v = nullptr;
@@ -91,6 +97,7 @@ struct Plan {
     bool has_conv_map = false;
     long long* d_job_cost = nullptr;        // deposit launch scratch [kMaxJobs + 1]
     double *d_contrib = nullptr, *d_red = nullptr;
+    float2* d_dvda = nullptr;               // backward: dv_los/d(inclination, azimuth) per particle [cap]
     float4* d_wu = nullptr;                 // backward: unit-mass weights [cap]
     float4* d_adjpart = nullptr;            // backward: per (tile, particle) sums [n_tiles][cap]
     Alloc alloc;

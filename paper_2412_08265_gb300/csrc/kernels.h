@@ -58,9 +58,12 @@ constexpr int kMaxBands = 32;
 // the plain spaxel key); particles outside the field get nx*ny*n_bands.
 struct AssignParams {
     long long n;
-    const float *x, *y, *z, *vy, *vz, *v_los;
+    const float *x, *y, *z, *vx, *vy, *vz, *v_los;  // vx nullable (treated as 0)
     int preprojected;
-    double cos_i, sin_i;
+    double R[9];      // orientation, row-major: x' = (R0 x + R1 y) + R2 z, ..., v_los = (R6 vx + R7 vy) + R8 vz
+    double Di[3];     // dv_los/d(inclination) = Di . (vx, vy, vz)
+    double Da[2];     // dv_los/d(azimuth) = Da . (vx, vy)
+    float2* dv_dang;  // [n] original order (nullable): (dv_los/d inclination, dv_los/d azimuth)
     double x_lo, y_lo, inv_size;
     int nx, ny;
     int* key;         // [n]
@@ -198,7 +201,8 @@ struct AdjointParams {
     double l0, dl, z_cosmo, flux_scale;
     const float* G0;           // [n_s][n_lambda] dL/dcube0
     float *d_mass, *d_age, *d_Z, *d_v;   // original order, nullable
-    double* contrib;           // [n_in][2] per sorted particle: dL/dv, m*dL/dm (FP64)
+    double* contrib;           // [n_in][kGlobal] per sorted particle: dL/dv, m*dL/dm, dL/dv * dv/d(incl), dL/dv * dv/d(azim)
+    const float2* dv_dang;     // [n] original order: dv_los/d(inclination), dv_los/d(azimuth)
     long long n_in;            // upper bound (grid sizing)
 };
 int launch_adjoint_rec(const AdjointParams& P, const DepRec* rec, cudaStream_t st);
@@ -236,6 +240,8 @@ int launch_adjoint_setup(const AdjointParams& P, const DepRec* rec, float4* wu, 
 // dL/d(mass, age, Z, v_los) in original order (+ contributions to global sums).
 int launch_adjoint_final(const AdjointParams& P, const float4* part, int n_tiles, long long n_cap, cudaStream_t st);
 int launch_zero_grads(float* a, float* b, float* c, float* d, long long n, cudaStream_t st);
-int launch_reduce_global(const double* contrib, const int* n_in_dev, double* out2, double* scratch, cudaStream_t st);
+// Gradients of the shared parameters: dL/dv_sys, dL/dln(M), dL/d(inclination), dL/d(azimuth).
+constexpr int kGlobal = 4;
+int launch_reduce_global(const double* contrib, const int* n_in_dev, double* out, double* scratch, cudaStream_t st);
 
 }  // namespace rubix

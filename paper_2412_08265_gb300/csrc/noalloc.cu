@@ -27,6 +27,7 @@
 #include "../../include/rubix.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "engine.h"
 
 namespace rubix {
 
@@ -116,8 +117,7 @@ extern "C" rubix_status rubix_spaxel_sort_noalloc(const rubix_particles* p, cons
     A.vz = nullptr;
     A.v_los = nullptr;
     A.preprojected = p->preprojected ? 1 : 0;
-    A.cos_i = std::cos(p->inclination);
-    A.sin_i = std::sin(p->inclination);
+    orientation_matrix(p->inclination, p->azimuth, p->position_angle, A.R, A.Di, A.Da);
     A.x_lo = (-0.5 * (double)tel->nx) * tel->spaxel_size;
     A.y_lo = (-0.5 * (double)tel->ny) * tel->spaxel_size;
     A.inv_size = 1.0 / tel->spaxel_size;

@@ -24,15 +24,18 @@ __global__ void k_assign(AssignParams P) {
             xp = (double)P.x[p];
             yp = (double)P.y[p];
             v = P.v_los ? (double)P.v_los[p] : 0.0;
+            if (P.dv_dang) P.dv_dang[p] = make_float2(0.f, 0.f);
         } else {
-            double a = __dmul_rn((double)P.y[p], P.cos_i);
-            double b = __dmul_rn((double)P.z[p], P.sin_i);
-            xp = (double)P.x[p];
-            yp = __dsub_rn(a, b);
+            // rotated position and velocity, each product and sum rounded once
+            const double X = (double)P.x[p], Y = (double)P.y[p], Z = (double)P.z[p];
+            xp = __dadd_rn(__dadd_rn(__dmul_rn(P.R[0], X), __dmul_rn(P.R[1], Y)), __dmul_rn(P.R[2], Z));
+            yp = __dadd_rn(__dadd_rn(__dmul_rn(P.R[3], X), __dmul_rn(P.R[4], Y)), __dmul_rn(P.R[5], Z));
             if (P.vy) {
-                double c = __dmul_rn((double)P.vy[p], P.sin_i);
-                double d = __dmul_rn((double)P.vz[p], P.cos_i);
-                v = __dadd_rn(c, d);
+                const double VX = P.vx ? (double)P.vx[p] : 0.0, VY = (double)P.vy[p], VZ = (double)P.vz[p];
+                v = __dadd_rn(__dadd_rn(__dmul_rn(P.R[6], VX), __dmul_rn(P.R[7], VY)), __dmul_rn(P.R[8], VZ));
+                if (P.dv_dang)
+                    P.dv_dang[p] = make_float2((float)(P.Di[0] * VX + P.Di[1] * VY + P.Di[2] * VZ),
+                                               (float)(P.Da[0] * VX + P.Da[1] * VY));
             } else {
                 v = 0.0;
             }

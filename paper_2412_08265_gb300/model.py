@@ -15,6 +15,10 @@ import torch
 from . import capi
 
 
+# keys of a particle dict that hold scalars, not arrays
+SCALAR_KEYS = ("preprojected", "inclination", "azimuth", "position_angle")
+
+
 def _dev_f32(a, device) -> torch.Tensor:
     if isinstance(a, torch.Tensor):
         return a.to(device=device, dtype=torch.float32).contiguous()
@@ -74,8 +78,8 @@ class CubeModel:
                 d[name] = _dev_f32(a, self.device)
         d["preprojected"] = bool(getattr(p, "preprojected", True) if not isinstance(p, dict)
                                  else p.get("preprojected", True))
-        d["inclination"] = float(getattr(p, "inclination", 0.0) if not isinstance(p, dict)
-                                 else p.get("inclination", 0.0))
+        for name in ("inclination", "azimuth", "position_angle"):
+            d[name] = float(getattr(p, name, 0.0) if not isinstance(p, dict) else p.get(name, 0.0))
         return d
 
     @staticmethod
@@ -89,12 +93,13 @@ class CubeModel:
         return capi.rubix_particles(n, ptr("x"), ptr("y"), ptr("z"), ptr("vx"), ptr("vy"), ptr("vz"),
                                     ptr("v_los"), ptr("mass"), ptr("age"), ptr("Z"),
                                     1 if on_device else 0, 1 if d.get("preprojected", True) else 0,
-                                    float(d.get("inclination", 0.0)))
+                                    float(d.get("inclination", 0.0)), float(d.get("azimuth", 0.0)),
+                                    float(d.get("position_angle", 0.0)))
 
     def forward(self, p, noise_seed: int = 0, noise_s2n: float = 0.0, out: torch.Tensor | None = None,
                 stream: torch.cuda.Stream | None = None) -> torch.Tensor:
         d = p if isinstance(p, dict) and all(isinstance(v, torch.Tensor) for k, v in p.items()
-                                             if k not in ("preprojected", "inclination")) \
+                                             if k not in SCALAR_KEYS) \
             else self.device_particles(p)
         if out is None:
             out = torch.empty(self.cube_shape, dtype=torch.float32, device=self.device)
@@ -109,7 +114,7 @@ class CubeModel:
                  stream: torch.cuda.Stream | None = None):
         n = int(self._last["mass"].shape[0])
         g = [torch.empty(n, dtype=torch.float32, device=self.device) for _ in range(4)]
-        glob = torch.empty(2, dtype=torch.float64, device=self.device) if want_global else None
+        glob = torch.empty(4, dtype=torch.float64, device=self.device) if want_global else None
         st = stream or torch.cuda.current_stream(self.device)
         dc = dL_dcube.to(torch.float32).contiguous()
         capi.rubix_cube_backward(self.handle, dc.data_ptr(), g[0].data_ptr(), g[1].data_ptr(),

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import capi
-from .model import CubeModel
+from .model import SCALAR_KEYS, CubeModel
 
 
 class Server:
@@ -34,10 +34,10 @@ class Server:
 
     def submit(self, tel, particles: dict, out: torch.Tensor, noise_seed: int = 0, noise_s2n: float = 0.0) -> int:
         """Queue a forward model of `particles` (dict of float32 tensors on this
-        device or on the host, plus 'preprojected' / 'inclination') into `out`
+        device or on the host, plus the scalars 'preprojected', 'inclination', 'azimuth', 'position_angle') into `out`
         (float32 [ny, nx, n_lambda], device or host)."""
         on_dev = [isinstance(v, torch.Tensor) and v.is_cuda for k, v in particles.items()
-                  if k not in ("preprojected", "inclination")]
+                  if k not in SCALAR_KEYS]
         if any(on_dev) != all(on_dev):
             raise ValueError("particle arrays must be all on the device or all on the host")
         cp = CubeModel.c_particles(particles, on_device=all(on_dev))
@@ -49,7 +49,7 @@ class Server:
     def footprint(self, tel, particles: dict, out: torch.Tensor) -> int:
         """Device bytes the request would hold on the GPU (admission counts these)."""
         on_dev = all(isinstance(v, torch.Tensor) and v.is_cuda for k, v in particles.items()
-                     if k not in ("preprojected", "inclination"))
+                     if k not in SCALAR_KEYS)
         cp = CubeModel.c_particles(particles, on_device=on_dev)
         return capi.rubix_serve_footprint(self.handle, CubeModel.c_telescope(tel), cp, 1 if out.is_cuda else 0)
 

@@ -155,3 +155,25 @@ def test_backward_bin_means(torch_cuda, case):
     rng = np.random.default_rng(13)
     G = rng.standard_normal((tel.ny, tel.nx, tel.n_lambda))
     _grad_check(torch_cuda, wl, G)
+
+
+@pytest.mark.parametrize("resample", [0, 1])
+def test_backward_oriented_3d_and_angle_gradients(torch_cuda, resample):
+    """3-D disk oriented by (inclination, azimuth, position angle): per-particle
+    gradients against the oracle, and the shared-angle gradients d_global[2:4]
+    = sum_p dL/dv_p dv_p/d(angle) against the oracle's sums in FP64."""
+    from paper_2412_08265_gb300.model import CubeModel
+    base = synth.small_galaxy()
+    p = synth.disk_3d(20_000, 33, inclination=1.1, azimuth=0.7, position_angle=-0.4)
+    tel = synth.Telescope(nx=40, ny=36, spaxel_size=0.35, n_lambda=900, lambda0=4050.0, dlambda=2.4,
+                          resample=resample)
+    wl = synth.Workload("oriented-3d", p, base.ssp, tel)
+    rng = np.random.default_rng(19)
+    G = rng.standard_normal((tel.ny, tel.nx, tel.n_lambda))
+    got, ref, glob, key = _grad_check(torch_cuda, wl, G)
+    _, _, _, di, da = oracle.orient(p, derivatives=True)
+    odv = ref[3]
+    for c, d in ((2, di), (3, da)):
+        exp = float((odv * d).sum())
+        assert abs(glob[c] - exp) <= 1e-4 * float(np.abs(odv * d).sum()), (c, glob[c], exp)
+        assert abs(exp) > 0.0

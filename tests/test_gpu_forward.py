@@ -74,7 +74,7 @@ def concat(a, b):
 # ---------------------------------------------------------------------------
 # a1/a2 keys and a3 sort: bit-exact
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("kind", ["small", "mid", "inclined"])
+@pytest.mark.parametrize("kind", ["small", "mid", "inclined", "euler"])
 def test_spaxel_keys_bit_exact(torch_cuda, kind):
     if kind == "small":
         wl = synth.small_galaxy()
@@ -84,10 +84,14 @@ def test_spaxel_keys_bit_exact(torch_cuda, kind):
         wl = synth.mid_galaxy(n=200_000)
         p = concat(wl.particles, edge_particles(wl.telescope, 512))
         tel = wl.telescope
-    else:
+    elif kind == "inclined":
         wl = synth.small_galaxy()
         tel = synth.serving_telescope(73)
         p = synth.disk_3d(50_000, 21, inclination=0.83)
+    else:
+        wl = synth.small_galaxy()
+        tel = synth.serving_telescope(73)
+        p = synth.disk_3d(50_000, 22, inclination=1.9, azimuth=-2.4, position_angle=0.61)
     model = make_model(wl.ssp, tel, n=p.n)
     got = model.spaxel_keys(p).cpu().numpy()
     xp, yp, _ = oracle.orient(p)
@@ -319,10 +323,12 @@ def test_reduced_precision_templates(torch_cuda, dtype):
     model.close()
 
 
-def test_inclined_3d_galaxy(torch_cuda):
+@pytest.mark.parametrize("angles", [(1.2, 0.0, 0.0), (2.2, 0.9, -1.3)])
+def test_inclined_3d_galaxy(torch_cuda, angles):
+    """3-D disk oriented by (inclination, azimuth, position angle)."""
     wl = synth.small_galaxy()
     tel = synth.Telescope(nx=48, ny=40, spaxel_size=0.3, n_lambda=700, lambda0=4050.0, dlambda=3.0)
-    p = synth.disk_3d(30_000, 31, inclination=1.2)
+    p = synth.disk_3d(30_000, 31, inclination=angles[0], azimuth=angles[1], position_angle=angles[2])
     model = make_model(wl.ssp, tel, n=p.n)
     got = model.forward(p).cpu().numpy()
     ref = oracle.forward(p, wl.ssp, tel, n_threads=NT)
