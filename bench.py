@@ -126,14 +126,14 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, target_s: float, seed: int = 123):
+def oracle_sample(wl, target_s: float, seed: int = 123, cores: int | None = None):
     """Time the oracle's deposit over a seeded set of spaxel neighbourhoods sized
     for roughly target_s seconds; returns (deposits/s, cores, description,
     centres, cube0 for the sample, key)."""
     import oracle
     tel = wl.telescope
     p = wl.particles
-    cores = os.cpu_count() or 1
+    cores = cores or os.cpu_count() or 1
     xp, yp, v = oracle.orient(p)
     key = oracle.spaxel_keys(xp, yp, tel)
     n_s = tel.nx * tel.ny
@@ -340,8 +340,21 @@ def run_extra(args, dev, flush):
     from paper_2412_08265_gb300.model import CubeModel
     stream = torch.cuda.current_stream(dev)
     out = {}
-    # differentiable step
+    sel = set(args.extra.split(","))
     wl = synth.mid_galaxy(n=args.particles, seed=1)
+    if "differentiable" in sel:
+        out["differentiable"] = _extra_differentiable(args, dev, flush, wl, stream)
+    if "bin_means" in sel:
+        out["bin_means"] = _extra_bin_means(args, dev, flush, wl, stream)
+    if "large_bf16" in sel:
+        out["large_bf16"] = _extra_large_bf16(args, dev, flush, stream)
+    return out
+
+
+def _extra_differentiable(args, dev, flush, wl, stream):
+    import torch
+    from paper_2412_08265_gb300 import synth
+    from paper_2412_08265_gb300.model import CubeModel
     tgt_p = synth.perturbed_target(wl.particles)
     model = CubeModel(wl.ssp, wl.telescope, "f32", max_particles=wl.particles.n, device=dev)
     target = model.forward(tgt_p).clone()
@@ -361,15 +374,21 @@ def run_extra(args, dev, flush):
     t_fwd = _events_ms(torch, lambda: model.forward(d, out=cube), stream, max(3, min(args.steps, 10)), flush)
     grads = res["grads"]
     ok = all(bool(torch.isfinite(x).all()) for x in grads[:4]) and bool(torch.isfinite(grads[4]).all())
-    out["differentiable"] = {
+    res = {
         "workload": "mid-disk-1e6p-150x150x3721-f32, loss 1/2|cube - target|^2, target: ages/Z x (1 + N(0, 0.1)), v + 20 km/s",
         "step_ms": float(np.median(t_step)), "forward_ms": float(np.median(t_fwd)),
         "backward_ms": float(np.median(t_step) - np.median(t_fwd)),
         "deposits_per_s_forward_plus_backward": 2.0 * n_dep / (float(np.median(t_step)) / 1e3),
         "grads_finite": ok}
     model.close()
-    del d, cube, target
-    # mid-size workload with flux-conserving bin means (resample = 1)
+    return res
+
+
+def _extra_bin_means(args, dev, flush, wl, stream):
+    """Mid-size workload with flux-conserving bin means (resample = 1)."""
+    import torch
+    from paper_2412_08265_gb300 import synth
+    from paper_2412_08265_gb300.model import CubeModel
     tel_m = synth.Telescope(**{**wl.telescope.__dict__, "resample": 1})
     model = CubeModel(wl.ssp, tel_m, "f32", max_particles=wl.particles.n, device=dev)
     d = model.device_particles(wl.particles)
@@ -381,14 +400,20 @@ def run_extra(args, dev, flush):
     t = _events_ms(torch, lambda: model.forward(d, out=cube), stream, max(3, min(args.steps, 10)), flush)
     dep = model.profile_history("deposit")
     model.set_profiling(False)
-    out["bin_means"] = {
+    res = {
         "workload": "mid-disk-1e6p-150x150x3721-f32, resample = 1 (mean over each output bin)",
         "ms_per_step": float(np.median(t)), "deposit_ms": float(np.median(dep)),
         "deposits_per_s": st["deposits"] / (float(np.median(t)) / 1e3),
         "slow_particle_tiles": st["slow_particle_tiles"]}
     model.close()
-    del d, cube
-    # large galaxy, BF16 templates
+    return res
+
+
+def _extra_large_bf16(args, dev, flush, stream):
+    """Large galaxy, BF16 templates."""
+    import torch
+    from paper_2412_08265_gb300 import synth
+    from paper_2412_08265_gb300.model import CubeModel
     wl = synth.large_galaxy()
     model = CubeModel(wl.ssp, wl.telescope, "bf16", max_particles=wl.particles.n, device=dev)
     d = model.device_particles(wl.particles)
@@ -401,13 +426,13 @@ def run_extra(args, dev, flush):
     dep = model.profile_history("deposit")
     psf = model.profile_history("psf_lsf")
     model.set_profiling(False)
-    out["large_bf16"] = {
+    res = {
         "workload": wl.name, "n_in_fov": st["n_in_fov"], "ms_per_step": float(np.median(t)),
         "deposits_per_s": st["deposits"] / (float(np.median(t)) / 1e3),
         "deposit_ms": float(np.median(dep)), "psf_lsf_ms": float(np.median(psf)),
         "tile_bins": st["tile_w"], "age_bands": st["n_bands"]}
     model.close()
-    return out
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -457,7 +482,8 @@ def run_ours(args):
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     dep_ms = model.profile_history("deposit")
-    stage_last = model.stage_times()
+    stage_med = {k: float(np.median(model.profile_history(k)[-args.steps:]))
+                 for k in ("assign_sort", "setup_items", "deposit", "combine", "psf_lsf", "forward")}
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -545,6 +571,9 @@ def run_ours(args):
         import oracle
         rate, cores, desc, centres, cube0, dep, dt = oracle_sample(wl, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        # the same oracle on one core, over a smaller sample
+        rate1, _, desc1, _, _, _, _ = oracle_sample(wl, max(2.0, args.cpu_seconds / 3), seed=321, cores=1)
+        cpu["single_core"] = {"value": rate1, "sample": desc1}
         ref = oracle.psf_lsf_at(cube0, wl.telescope, centres[: min(len(centres), 24)])
         got = out.reshape(-1, wl.telescope.n_lambda)[torch.from_numpy(centres[: min(len(centres), 24)]).long().to(dev)]
         got = got.cpu().numpy().astype(np.float64)
@@ -562,7 +591,7 @@ def run_ours(args):
             "particles_per_s": n_in_all / total_s,
             "clocks": clk, "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "stage_ms_last_step": stage_last}
+            "stage_ms_median": stage_med}
     if not args.no_extra:
         line["workloads"] = run_extra(args, dev, flush)
     if args.serve_requests > 0:
@@ -584,6 +613,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--particles", type=int, default=1_000_000,
                     help="particles of the mid-size galaxy (smaller only for profiler captures)")
+    ap.add_argument("--extra", default="differentiable,bin_means,large_bf16",
+                    help="comma-separated extra workloads reported under 'workloads'")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the differentiable-step and large-galaxy measurements")
     ap.add_argument("--serve-requests", type=int, default=2000,

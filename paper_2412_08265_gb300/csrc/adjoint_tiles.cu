@@ -9,13 +9,15 @@
 //   slz = sum_j G_j dS_j/dtz                 (to Z outside)
 //   sv  = sum_j G_j dS_j/dt * (t_j + ls0/dls) (times dt/dv / t_abs outside)
 // dS/dta and dS/dtz are bilinear forms in the same four corners with weights
-// a = (-(1-tz), 1-tz, -tz, tz) and b = (-(1-ta), -ta, 1-ta, ta), so each is
-// one more dot product with the quad of the node. The deposit's (tile, work
-// item, age band) partition, quad slabs and 31-bin rounds carry over
-// unchanged: lane l forms M, A, B at node K0 + o_r + l, the neighbour node's
-// three values arrive by shuffle, and the lane accumulates G_j times the
-// interpolated values over its bins. A warp reduction per (particle, tile)
-// gives part[tile][particle]; K8 adds the tiles in FP64 in tile order.
+// a = (-(1-tz), 1-tz, -tz, tz) and b = (-(1-ta), -ta, 1-ta, ta). All three
+// forms are linear in the corner templates, so the lanes accumulate per
+// corner (G_j times the interpolated corner template, and G_j times the
+// corner's slope times the bin position) and apply w, a and b once per
+// particle and tile. The deposit's (tile, work item, age band) partition,
+// quad slabs and 31-bin rounds carry over unchanged: lane l reads the quad at
+// node K0 + o_r + l and the neighbour node's quad arrives by shuffle. A warp
+// reduction per (particle, tile) gives part[tile][particle]; K8 adds the
+// tiles in FP64 in tile order.
 #include "common.cuh"
 #include "kernels.h"
 #include "tile.cuh"
@@ -58,9 +60,12 @@ struct AdjSums {
 
 // General path: bins of this tile one at a time, quads from the slab when
 // every bin of the warp has its node pair there, else from global memory.
+// It reads dL/dcube0 from the spaxel's row (grow) itself, so that the fast
+// path's register copy never has to be kept in memory for this call.
 template <int R>
 __device__ __noinline__ AdjSums adj_general(const float4 w, const float4 g4, const TileCtx C, const float4* slab,
-                                            const float4* quad, int lane, const float (&G)[R], float ls0_over) {
+                                            const float4* quad, int lane, const float* __restrict__ grow,
+                                            float ls0_over) {
     const int c0_bi = __float_as_int(g4.x);
     const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
     bool ok = C.slab_w > 0 && (unsigned)(cell - C.cell0) < (unsigned)C.ncb;
@@ -94,7 +99,7 @@ __device__ __noinline__ AdjSums adj_general(const float4 w, const float4 g4, con
         const float m0 = quad_dot(w, q0), m1 = quad_dot(w, q1);
         const float a0 = s01 * (q0.y - q0.x) + s23 * (q0.w - q0.z), a1 = s01 * (q1.y - q1.x) + s23 * (q1.w - q1.z);
         const float b0 = s02 * (q0.z - q0.x) + s13 * (q0.w - q0.y), b1 = s02 * (q1.z - q1.x) + s13 * (q1.w - q1.y);
-        const float Gj = G[r];
+        const float Gj = grow[j];
         S.sm = fmaf(Gj, fmaf(f, m1 - m0, m0), S.sm);
         S.sa = fmaf(Gj, fmaf(f, a1 - a0, a0), S.sa);
         S.sz = fmaf(Gj, fmaf(f, b1 - b0, b0), S.sz);
@@ -103,10 +108,19 @@ __device__ __noinline__ AdjSums adj_general(const float4 w, const float4 g4, con
     return S;
 }
 
+// Fast path. The three weighted forms are linear in the corner templates,
+// so the rounds accumulate per corner c, in packed FP32x2 pairs (c = 0, 1 and
+// 2, 3): U_c = sum_j G_j V_c(j), V_c(j) the corner template interpolated at
+// bin j, and T_c = sum_j G_j u_j (T_c[hi] - T_c[lo]), the slope between the
+// bracketing nodes times the bin's absolute position u_j = t_j + ls0/dls.
+// Lane l reads node K0 + o_r + l's quad and takes the neighbouring node's
+// from lane l -+ 1 (four shuffles). Afterwards sm = w.U, sa = a.U, sz = b.U
+// and sv = w.T.
 template <int R>
 __device__ __forceinline__ AdjSums adj_particle(const float4 w, const float4 g4, const TileCtx& C,
                                                 const float4* __restrict__ slab, const float4* __restrict__ quad,
-                                                int lane, float lanef, const float (&G)[R], float ls0_over) {
+                                                int lane, float lanef, const float (&G)[R], const float* grow,
+                                                float ls0_over) {
     const int c0_bi = __float_as_int(g4.x);
     const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
     float f;
@@ -116,87 +130,49 @@ __device__ __forceinline__ AdjSums adj_particle(const float4 w, const float4 g4,
     const int cr = cell - C.cell0;
     if (!(delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R) &&
           (unsigned)cr < (unsigned)C.ncb))
-        return adj_general<R>(w, g4, C, slab, quad, lane, G, ls0_over);
-    const float s01 = w.x + w.y, s23 = w.z + w.w, s02 = w.x + w.z, s13 = w.y + w.w;
+        return adj_general<R>(w, g4, C, slab, quad, lane, grow, ls0_over);
     const float4* q = slab + (kw + lane) * C.ncb + cr;
     const int s31 = 31 * C.ncb, s30 = 30 * C.ncb;
     const float nld = -lanef * delta;
     const float d31 = 31.f * delta;
-    float tb = ((float)K0 + lanef) + ls0_over;  // absolute node position of lane l's node, / dls
-    AdjSums S{0.f, 0.f, 0.f, 0.f};
-#if RUBIX_DEP_PAIR2
-    // dS/dta and dS/dtz as quad dot products with the weight vectors a and b;
-    // rounds two at a time, partial sums in packed FP32x2 (one lane per round)
-    const float4 wa = make_float4(-s01, s01, -s23, s23), wb = make_float4(-s02, -s13, s02, s13);
-    float2 sm2 = make_float2(0.f, 0.f), sa2 = sm2, sz2 = sm2, sv2 = sm2;
-#pragma unroll
-    for (int r = 0; r + 1 < R; r += 2) {
-        const float4 Qa = *q;
-        const float fa = f, ta = tb;
-        f -= d31;
-        bool carry = f < 0.f;
-        f = carry ? f + 1.f : f;
-        q += carry ? s30 : s31;
-        tb += carry ? 30.f : 31.f;
-        const float4 Qb = *q;
-        const float fb = f, tbb = tb;
-        f -= d31;
-        carry = f < 0.f;
-        f = carry ? f + 1.f : f;
-        q += carry ? s30 : s31;
-        tb += carry ? 30.f : 31.f;
-        const float2 M = make_float2(quad_dot(w, Qa), quad_dot(w, Qb));
-        const float2 A = make_float2(quad_dot(wa, Qa), quad_dot(wa, Qb));
-        const float2 B = make_float2(quad_dot(wb, Qa), quad_dot(wb, Qb));
-        const float2 g = __fadd2_rn(make_float2(fa, fb), make_float2(nld, nld));
-        const int srca = g.x < 0.f ? lane - 1 : lane + 1, srcb = g.y < 0.f ? lane - 1 : lane + 1;
-        const float2 XM = make_float2(__shfl_sync(0xffffffffu, M.x, srca), __shfl_sync(0xffffffffu, M.y, srcb));
-        const float2 XA = make_float2(__shfl_sync(0xffffffffu, A.x, srca), __shfl_sync(0xffffffffu, A.y, srcb));
-        const float2 XB = make_float2(__shfl_sync(0xffffffffu, B.x, srca), __shfl_sync(0xffffffffu, B.y, srcb));
-        const float2 ag = make_float2(fabsf(g.x), fabsf(g.y));
-        const float2 G2 = make_float2(G[r], G[r + 1]);
-        const float2 dM = __fadd2_rn(XM, make_float2(-M.x, -M.y));
-        sm2 = __ffma2_rn(G2, __ffma2_rn(ag, dM, M), sm2);
-        sa2 = __ffma2_rn(G2, __ffma2_rn(ag, __fadd2_rn(XA, make_float2(-A.x, -A.y)), A), sa2);
-        sz2 = __ffma2_rn(G2, __ffma2_rn(ag, __fadd2_rn(XB, make_float2(-B.x, -B.y)), B), sz2);
-        // slope between the bracketing nodes, times the bin's node position
-        const float2 sl = make_float2(g.x < 0.f ? -dM.x : dM.x, g.y < 0.f ? -dM.y : dM.y);
-        sv2 = __ffma2_rn(__fmul2_rn(G2, sl), __fadd2_rn(make_float2(ta, tbb), g), sv2);
-    }
-    S.sm = sm2.x + sm2.y;
-    S.sa = sa2.x + sa2.y;
-    S.sz = sz2.x + sz2.y;
-    S.sv = sv2.x + sv2.y;
-#pragma unroll
-    for (int r = R & ~1; r < R; ++r) {
-#else
+    const float A = 1.f - delta;
+    // absolute position of bin j0 + 31 r + l, advanced by 31 A per round
+    float u = fmaf(lanef, A, ((float)K0 + f) + ls0_over);
+    const float du = 31.f * A;
+    float2 U01 = make_float2(0.f, 0.f), U23 = U01, T01 = U01, T23 = U01;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-#endif
         const float4 Q = *q;
-        const float M = quad_dot(w, Q);
-        const float A = s01 * (Q.y - Q.x) + s23 * (Q.w - Q.z);
-        const float B = s02 * (Q.z - Q.x) + s13 * (Q.w - Q.y);
         const float g = f + nld;
         const bool neg = g < 0.f;
         const int src = neg ? lane - 1 : lane + 1;
-        const float XM = __shfl_sync(0xffffffffu, M, src);
-        const float XA = __shfl_sync(0xffffffffu, A, src);
-        const float XB = __shfl_sync(0xffffffffu, B, src);
+        const float2 X01 = make_float2(__shfl_sync(0xffffffffu, Q.x, src), __shfl_sync(0xffffffffu, Q.y, src));
+        const float2 X23 = make_float2(__shfl_sync(0xffffffffu, Q.z, src), __shfl_sync(0xffffffffu, Q.w, src));
+        const float2 Q01 = make_float2(Q.x, Q.y), Q23 = make_float2(Q.z, Q.w);
+        const float2 D01 = __fadd2_rn(X01, make_float2(-Q.x, -Q.y));
+        const float2 D23 = __fadd2_rn(X23, make_float2(-Q.z, -Q.w));
         const float ag = fabsf(g);
+        const float2 ag2 = make_float2(ag, ag);
         const float Gj = G[r];  // 0 for lane 31 and bins past the end
-        const float dM = XM - M;
-        S.sm = fmaf(Gj, fmaf(ag, dM, M), S.sm);
-        S.sa = fmaf(Gj, fmaf(ag, XA - A, A), S.sa);
-        S.sz = fmaf(Gj, fmaf(ag, XB - B, B), S.sz);
-        // slope between the bracketing nodes, times the bin's node position
-        S.sv = fmaf(Gj * (neg ? -dM : dM), tb + g, S.sv);
+        const float2 G2 = make_float2(Gj, Gj);
+        U01 = __ffma2_rn(G2, __ffma2_rn(ag2, D01, Q01), U01);
+        U23 = __ffma2_rn(G2, __ffma2_rn(ag2, D23, Q23), U23);
+        const float gu = (neg ? -Gj : Gj) * u;  // D points from this node to the neighbour
+        const float2 gu2 = make_float2(gu, gu);
+        T01 = __ffma2_rn(gu2, D01, T01);
+        T23 = __ffma2_rn(gu2, D23, T23);
         f -= d31;
         const bool carry = f < 0.f;
         f = carry ? f + 1.f : f;
         q += carry ? s30 : s31;
-        tb += carry ? 30.f : 31.f;
+        u += du;
     }
+    const float s01 = w.x + w.y, s23 = w.z + w.w, s02 = w.x + w.z, s13 = w.y + w.w;
+    AdjSums S;
+    S.sm = fmaf(w.x, U01.x, fmaf(w.y, U01.y, fmaf(w.z, U23.x, w.w * U23.y)));
+    S.sa = fmaf(s01, U01.y - U01.x, s23 * (U23.y - U23.x));
+    S.sz = fmaf(s02, U23.x - U01.x, s13 * (U23.y - U01.y));
+    S.sv = fmaf(w.x, T01.x, fmaf(w.y, T01.y, fmaf(w.z, T23.x, w.w * T23.y)));
     return S;
 }
 
@@ -258,7 +234,7 @@ __device__ __noinline__ AdjSums adj_mean_bin(const float4 w, const float4 wa, co
 // has its nodes there, else from global memory.
 template <int R>
 __device__ __noinline__ AdjSums adj_mean_general(const float4 w, const float4 g4, const TileCtx C, const float4* slab,
-                                                 const float4* quad, int lane, const float (&G)[R + 1],
+                                                 const float4* quad, int lane, const float* __restrict__ grow,
                                                  float ls0_over) {
     const int c0_bi = __float_as_int(g4.x);
     const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
@@ -281,7 +257,7 @@ __device__ __noinline__ AdjSums adj_mean_general(const float4 w, const float4 g4
     for (int r = 0; r <= R; ++r) {
         const int j = C.j0 + 30 * r + lane;
         if (!(lane < (r < R ? 30 : R) && j < C.n_lambda)) continue;
-        const AdjSums b = adj_mean_bin(w, wa, wb, g4, C, j, G[r], use_slab, slab, quad, ls0_over);
+        const AdjSums b = adj_mean_bin(w, wa, wb, g4, C, j, grow[j], use_slab, slab, quad, ls0_over);
         S.sm += b.sm;
         S.sa += b.sa;
         S.sz += b.sz;
@@ -296,7 +272,7 @@ template <int R>
 __device__ __forceinline__ AdjSums adj_mean_particle(const float4 w, const float4 g4, const TileCtx& C,
                                                      const float4* __restrict__ slab,
                                                      const float4* __restrict__ quad, int lane, float lanef,
-                                                     const float (&G)[R + 1], float ls0_over) {
+                                                     const float (&G)[R + 1], const float* grow, float ls0_over) {
     const int c0_bi = __float_as_int(g4.x);
     const int cell = rec_c0(c0_bi), bi = rec_bi(c0_bi);
     float f;
@@ -306,7 +282,7 @@ __device__ __forceinline__ AdjSums adj_mean_particle(const float4 w, const float
     const int cr = cell - C.cell0;
     if (!(delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R - 1) &&
           (unsigned)cr < (unsigned)C.ncb))
-        return adj_mean_general<R>(w, g4, C, slab, quad, lane, G, ls0_over);
+        return adj_mean_general<R>(w, g4, C, slab, quad, lane, grow, ls0_over);
     const float s01 = w.x + w.y, s23 = w.z + w.w, s02 = w.x + w.z, s13 = w.y + w.w;
     const float4 wa = make_float4(-s01, s01, -s23, s23), wb = make_float4(-s02, -s13, s02, s13);
     const float4* q = slab + (kw + lane) * C.ncb + cr;
@@ -470,10 +446,23 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
                         AdjSums S;
                         if constexpr (MEAN)
                             S = adj_mean_particle<R>(P.wu[q], rec4[2 * q + 1], C, slab, P.quad, lane, lanef, G,
-                                                     P.ls0_over);
+                                                     grow, P.ls0_over);
                         else
-                            S = adj_particle<R>(P.wu[q], rec4[2 * q + 1], C, slab, P.quad, lane, lanef, G,
+                            S = adj_particle<R>(P.wu[q], rec4[2 * q + 1], C, slab, P.quad, lane, lanef, G, grow,
                                                 P.ls0_over);
+#if RUBIX_ADJ_XRED
+                        // the four sums over the warp with 6 shuffles: halves of the
+                        // warp trade pairs, quarters trade singles, then a butterfly
+                        // over 8 lanes; lane 8 v ends with sum v (v = sm, sa, sz, sv)
+                        const bool hi16 = lane >= 16, hi8 = (lane & 8) != 0;
+                        const float r0 = __shfl_xor_sync(0xffffffffu, hi16 ? S.sm : S.sz, 16);
+                        const float r1 = __shfl_xor_sync(0xffffffffu, hi16 ? S.sa : S.sv, 16);
+                        const float b0 = (hi16 ? S.sz : S.sm) + r0, b1 = (hi16 ? S.sv : S.sa) + r1;
+                        float c = (hi8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, hi8 ? b0 : b1, 8);
+#pragma unroll
+                        for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                        if ((lane & 7) == 0) reinterpret_cast<float*>(part + q)[lane >> 3] = c;
+#else
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) {
                             S.sm += __shfl_xor_sync(0xffffffffu, S.sm, o);
@@ -482,6 +471,7 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
                             S.sv += __shfl_xor_sync(0xffffffffu, S.sv, o);
                         }
                         if (lane == 0) part[q] = make_float4(S.sm, S.sa, S.sz, S.sv);
+#endif
                     }
                 }
             }

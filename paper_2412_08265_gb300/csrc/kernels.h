@@ -39,17 +39,22 @@ constexpr int kMaxBands = 32;
 #ifndef RUBIX_DEP_BANDS
 #define RUBIX_DEP_BANDS 0
 #endif
-// How later age bands add to a row the first band wrote: 0 = load, add,
-// store (the row prefetched to L2 when the item starts); 1 = in-order
-// reductions at L2.
 // 1: the fast path's rounds two at a time in packed FP32x2 arithmetic.
 #ifndef RUBIX_DEP_PAIR2
 #define RUBIX_DEP_PAIR2 1
+#endif
+// 1: the adjoint's four per-particle sums reduced over the warp with 6
+// shuffles (pairs, then singles, then a butterfly); 0: 20 (one butterfly each).
+#ifndef RUBIX_ADJ_XRED
+#define RUBIX_ADJ_XRED 1
 #endif
 // Work items a warp claims at once (its first lanes look them up together).
 #ifndef RUBIX_DEP_GRAB
 #define RUBIX_DEP_GRAB 4
 #endif
+// How later age bands add to a row the first band wrote: 0 = load, add,
+// store (the row prefetched to L2 when the item starts); 1 = in-order
+// reductions at L2.
 #ifndef RUBIX_DEP_BANDADD
 #define RUBIX_DEP_BANDADD 1
 #endif

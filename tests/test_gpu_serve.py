@@ -71,7 +71,7 @@ def run_all(torch, srv, reqs, noise=None):
 
 def test_serve_alone_vs_mix_bitwise_and_vs_handle(env):
     torch, ssp = env
-    reqs = requests(20)
+    reqs = requests(50)
     noise = [(7 + i, 30.0) if i % 4 == 3 else (0, 0.0) for i in range(len(reqs))]
     # alone: one slot, one galaxy per deposit launch, one request at a time
     srv = server(ssp, slots=1, batch=1)
@@ -83,7 +83,7 @@ def test_serve_alone_vs_mix_bitwise_and_vs_handle(env):
     assert st["ok"] == len(reqs) and st["deposit_launches"] == len(reqs) and st["max_batch"] == 1
     srv.close()
     # mix: everything submitted at once, shared deposit launches
-    srv = server(ssp, slots=16, batch=16)
+    srv = server(ssp, budget=24 << 30, slots=16, batch=16)
     mix, _ = run_all(torch, srv, reqs, noise=noise)
     st = srv.stats()
     assert st["ok"] == len(reqs) and st["failed"] == 0
@@ -102,16 +102,41 @@ def test_serve_alone_vs_mix_bitwise_and_vs_handle(env):
         assert np.array_equal(got.view(np.uint32), mix[i].view(np.uint32)), i
 
 
-def test_served_request_matches_oracle(env):
+def test_served_requests_match_oracle(env):
+    """20 served requests against the oracle: 19 of 1e3-1e5 particles and
+    10-48 spaxels a side on the whole cube (the smallest request included),
+    and a 2e6-particle 300x300 request at sampled spaxels (neighbourhoods of
+    the densest spaxels, random ones and the field corners)."""
     torch, ssp = env
-    reqs = requests(6, seed=9, n_lo=1e3, n_hi=2e4, side_lo=10, side_hi=24)
-    srv = server(ssp)
+    reqs = requests(19, seed=9, n_lo=1e3, n_hi=1e5, side_lo=10, side_hi=48)
+    big_tel = synth.serving_telescope(300)
+    big = synth.disk_3d(2_000_000, 77, inclination=0.9)
+    reqs.append((big, big_tel))
+    srv = server(ssp, budget=16 << 30)
     outs, _ = run_all(torch, srv, reqs)
     srv.close()
-    for (p, tel), got in zip(reqs[:3], outs[:3]):
+    assert min(p.n for p, _ in reqs[:19]) < 2e3
+    for (p, tel), got in zip(reqs[:19], outs[:19]):
         ref = oracle.forward(p, ssp, tel, n_threads=NT)
         err = float(np.abs(got.astype(np.float64) - ref).max() / np.abs(ref).max())
         assert err <= TOL_F32
+    # the large request at sampled spaxels
+    xp, yp, v = oracle.orient(big)
+    key = oracle.spaxel_keys(xp, yp, big_tel)
+    ns = big_tel.nx * big_tel.ny
+    counts = np.bincount(key, minlength=ns + 1)[:ns]
+    rng = np.random.default_rng(3)
+    sel = np.unique(np.concatenate([np.argsort(counts)[-3:], rng.choice(np.flatnonzero(counts > 0), 5, replace=False),
+                                    [0, big_tel.nx - 1, ns - 1]])).astype(np.int32)
+    mask = np.zeros(ns, np.uint8)
+    for s_ in sel:
+        y, x = divmod(int(s_), big_tel.nx)
+        for yy in range(max(0, y - 3), min(big_tel.ny, y + 4)):
+            mask[yy * big_tel.nx + max(0, x - 3): yy * big_tel.nx + min(big_tel.nx, x + 4)] = 1
+    cube0 = oracle.deposit(key, v, big, ssp, big_tel, mask=mask, n_threads=NT)
+    ref = oracle.psf_lsf_at(cube0, big_tel, sel)
+    got = outs[19].reshape(-1, big_tel.n_lambda)[sel].astype(np.float64)
+    assert float(np.abs(got - ref).max()) / float(np.abs(ref).max()) <= TOL_F32
 
 
 def test_host_inputs_and_outputs(env):

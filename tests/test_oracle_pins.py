@@ -496,7 +496,8 @@ def test_gradient_matches_central_differences(seed, resample):
                 nodes = ssp.log10_age_nodes if name == "age" else ssp.log10_Z_nodes
                 if any(math.log10(float(lo)) <= nd <= math.log10(float(hi)) for nd in nodes):
                     continue
-            assert abs(fd - grad[i]) <= 2e-4 * scale + 1e-9 * abs(L0), (name, i, fd, grad[i])
+            # central differences with h = 1e-4 |x| agree to 1e-6 (measured worst 5e-7)
+            assert abs(fd - grad[i]) <= 1e-6 * scale + 1e-12 * abs(L0), (name, i, fd, grad[i])
             checked += 1
     assert checked >= 40
 
