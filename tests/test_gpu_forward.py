@@ -418,7 +418,8 @@ def test_forward_redshifted_and_scaled(torch_cuda, z):
 
 # ---------------------------------------------------------------------------
 # a5 flux-conserving alternative: bin means (resample = 1)
-@pytest.mark.parametrize("case", ["fast", "redshift_general", "coarse_bins", "fine_bins", "high_velocity"])
+@pytest.mark.parametrize("case", ["fast", "redshift_general", "coarse_bins", "fine_bins", "tiny_bins",
+                                  "high_velocity"])
 def test_forward_bin_means(torch_cuda, case):
     """Bin means against the oracle. "fast": dt/dj in (30/31, 1], every particle
     on the 30-bin-round path; "redshift_general" (dt/dj < 30/31) and the coarse
@@ -434,6 +435,9 @@ def test_forward_bin_means(torch_cuda, case):
         kw.update(n_lambda=1583, dlambda=2.9, lambda0=4760.0)
     elif case == "fine_bins":
         kw.update(n_lambda=1237, dlambda=0.8125, lambda0=4751.3)
+    elif case == "tiny_bins":
+        # 0.04 of a template step per bin: every bin's interval inside one segment
+        kw.update(n_lambda=2000, dlambda=0.05, lambda0=6000.0, lsf_sigma=0.2)
     elif case == "high_velocity":
         p.v_los = p.v_los.copy()
         p.v_los[::9] = np.float32(4000.0)
@@ -449,9 +453,33 @@ def test_forward_bin_means(torch_cuda, case):
         assert st["slow_particle_tiles"] == 0
     if case == "high_velocity":
         assert st["slow_particle_tiles"] > 0
-    # not the centre samples
+    # not the centre samples (except on bins much finer than the template step)
     lin = oracle.forward(p, base.ssp, synth.Telescope(**{**kw, "resample": 0}), n_threads=NT)
-    assert float(np.abs(lin - ref).max()) > 100 * TOL_F32 * float(np.abs(ref).max())
+    if case != "tiny_bins":
+        assert float(np.abs(lin - ref).max()) > 100 * TOL_F32 * float(np.abs(ref).max())
+    model.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_bin_means_reduced_precision_templates(torch_cuda, dtype):
+    """Bin means with BF16/FP16 templates: against the oracle on the original
+    templates (reduced-precision tolerance, also on total flux) and on the
+    rounded templates (FP32 tolerance)."""
+    base = synth.mid_galaxy(n=30_000, seed=23)
+    tel = synth.Telescope(nx=20, ny=20, spaxel_size=0.5, n_lambda=3721, lambda0=4750.0, dlambda=1.25,
+                          resample=1)
+    p = base.particles
+    model = make_model(base.ssp, tel, dtype=dtype, n=p.n)
+    got = model.forward(p).cpu().numpy()
+    ref = oracle.forward(p, base.ssp, tel, n_threads=NT)
+    assert rel_err(got, ref) <= TOL_BF16
+    assert abs(got.sum() / ref.sum() - 1.0) <= TOL_BF16
+    if dtype == "bf16":
+        rounded = bf16_round(base.ssp.spectra)
+    else:
+        rounded = np.asarray(base.ssp.spectra, dtype=np.float32).astype(np.float16).astype(np.float64)
+    refq = oracle.forward(p, base.ssp, tel, n_threads=NT, spectra=rounded)
+    assert rel_err(got, refq) <= TOL_F32
     model.close()
 
 
