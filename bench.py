@@ -309,6 +309,8 @@ def run_serving(args, dev, ssp):
                                 "deposit_launches": st["deposit_launches"], "max_batch": st["max_batch"],
                                 "peak_bytes": st["peak_bytes"]}
     clk = clocks.stop()
+    del ins, mothers
+    res["classes"] = _serve_classes(torch, server, dev, args)
     return {"requests": n_req, "arrival_rate_hz": rate, "load_vs_sequential_capacity": args.serve_load,
             "particles": "log-uniform [1e4, 2e7] (prefixes of 4 device-drawn 3-D disks)",
             "cube_side": "uniform [40, 300] spaxels of 0.2 kpc x 3721 bins",
@@ -316,6 +318,44 @@ def run_serving(args, dev, ssp):
             "voxels_total": float(vox.sum()), "max_slots": args.serve_slots, "max_batch": args.serve_batch,
             "hbm_budget_bytes": budget, "latency": "arrival to completion seen by the client",
             "clocks": clk, **res}
+
+
+def _serve_classes(torch, server, dev, args):
+    """The two ends of the request mix, each as a saturated stream through the
+    served configuration: small galaxies in large cubes (HBM-bound: the
+    deposit writes every voxel, the PSF/LSF reads and writes it again, 12 B per
+    voxel) and large galaxies in small cubes (the deposit's FP32 work, 16 flop
+    per deposit); each with its fraction of the matching peak."""
+    from paper_2412_08265_gb300 import synth
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    props = torch.cuda.get_device_properties(dev)
+    fp32 = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    out = {}
+    for name, n_p, side, count in (("small_galaxy_large_cube", 10_000, 300, 24),
+                                   ("large_galaxy_small_cube", 20_000_000, 40, 8)):
+        d = synth.disk_3d_device(n_p, 7100 + side, dev)
+        d["preprojected"] = False
+        d["inclination"] = 0.5
+        half = 0.5 * side * SERVE_SPAXEL_KPC
+        x = d["x"].double()
+        yp = d["y"].double() * math.cos(0.5) - d["z"].double() * math.sin(0.5)
+        n_in = int(((x >= -half) & (x < half) & (yp >= -half) & (yp < half)).sum())
+        reqs = [{"side": side} for _ in range(count)]
+        srv = server(args.serve_slots, args.serve_batch)
+        _drive(torch, srv, dev, reqs[:2], [d] * 2, np.zeros(2))
+        _, mk = _drive(torch, srv, dev, reqs, [d] * count, np.zeros(count))
+        srv.close()
+        deposits = float(count) * n_in * 3721
+        voxels = float(count) * side * side * 3721
+        gbs = 12.0 * voxels / mk / 1e9
+        tfl = 16.0 * deposits / mk / 1e12
+        out[name] = {"requests": count, "particles": n_p, "cube_side": side, "makespan_s": mk,
+                     "requests_per_s": count / mk, "deposits_per_s": deposits / mk,
+                     "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / hbm,
+                     "fp32_tflops": tfl, "fp32_frac": tfl / fp32}
+        del d
+    return out
 
 
 # ---------------------------------------------------------------------------
