@@ -40,7 +40,7 @@ struct SspState {
     size_t dep_smem = 0;
     int* d_tile_klo = nullptr;
     CUtensorMap tmap{};
-    int dep_ctas = 0, dep_threads = RUBIX_DEP_THREADS, chunk = RUBIX_DEP_CHUNK, cost_c0 = 2;
+    int dep_ctas = 0, dep_threads = RUBIX_DEP_THREADS, chunk = RUBIX_DEP_CHUNK, cost_c0 = RUBIX_DEP_COSTC0;
     unsigned* d_err = nullptr;              // device error word (kernel bit flags)
     unsigned long long* d_slow = nullptr;   // (particle, tile) pairs on the global-memory path
 };

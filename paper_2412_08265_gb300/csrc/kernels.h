@@ -28,7 +28,7 @@ constexpr int kMaxBands = 32;
 // wavelength tile, and a fixed number of age bands (0 = chosen by the cost
 // estimate).
 #ifndef RUBIX_DEP_CHUNK
-#define RUBIX_DEP_CHUNK 1024
+#define RUBIX_DEP_CHUNK 256
 #endif
 #ifndef RUBIX_DEP_VHALO
 #define RUBIX_DEP_VHALO 800.0
@@ -47,6 +47,11 @@ constexpr int kMaxBands = 32;
 // shuffles (pairs, then singles, then a butterfly); 0: 20 (one butterfly each).
 #ifndef RUBIX_ADJ_XRED
 #define RUBIX_ADJ_XRED 1
+#endif
+// Cost of a work item in particle units, for the static split of the
+// (tile, item) cost space over CTAs.
+#ifndef RUBIX_DEP_COSTC0
+#define RUBIX_DEP_COSTC0 4
 #endif
 // Work items a warp claims at once (its first lanes look them up together).
 #ifndef RUBIX_DEP_GRAB
