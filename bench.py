@@ -36,7 +36,7 @@ REL_ERR_BOUND = 1e-5
 # DRAM bytes (read + write) per deposit launch on the mid-size workload (1e6
 # particles), from the ncu capture summarised in profiles/k_deposit_mid-disk-1e6p.md;
 # None when the kernel or the workload differs from that capture.
-DEPOSIT_TRAFFIC_BYTES = 2.481773e9 + 2.719713e9
+DEPOSIT_TRAFFIC_BYTES = 2.515222e9 + 2.767698e9
 
 
 def dist_env():
