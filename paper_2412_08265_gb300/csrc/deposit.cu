@@ -745,19 +745,8 @@ __global__ void k_combine(const int* __restrict__ part_off, int n_s, int n_lambd
         const int p0 = part_off[s], p1 = part_off[s + 1];
         if (p1 <= p0) continue;
         for (int j = threadIdx.x; j < n_lambda; j += blockDim.x) {
-            // four rows' loads in flight at once, added in item order
-            const float* __restrict__ col = partials + j;
             double acc = 0.0;
-            int r = p0;
-            for (; r + 4 <= p1; r += 4) {
-                const float a = col[(long long)r * n_lambda], b = col[(long long)(r + 1) * n_lambda];
-                const float c = col[(long long)(r + 2) * n_lambda], d = col[(long long)(r + 3) * n_lambda];
-                acc += (double)a;
-                acc += (double)b;
-                acc += (double)c;
-                acc += (double)d;
-            }
-            for (; r < p1; ++r) acc += (double)col[(long long)r * n_lambda];
+            for (int r = p0; r < p1; ++r) acc += (double)partials[(long long)r * n_lambda + j];
             cube[(long long)s * pitch + j] = (float)acc;
         }
     }
