@@ -440,10 +440,17 @@ def _extra_bin_means(args, dev, flush, wl, stream):
     t = _events_ms(torch, lambda: model.forward(d, out=cube), stream, max(3, min(args.steps, 10)), flush)
     dep = model.profile_history("deposit")
     model.set_profiling(False)
+    # the backward of the same forward, for a fixed cotangent
+    g = torch.randn(model.cube_shape, generator=torch.Generator(device=dev).manual_seed(5), device=dev)
+    model.forward(d, out=cube)
+    for _ in range(2):
+        model.backward(g)
+    tb = _events_ms(torch, lambda: model.backward(g), stream, max(3, min(args.steps, 10)), flush)
     res = {
         "workload": "mid-disk-1e6p-150x150x3721-f32, resample = 1 (mean over each output bin)",
         "ms_per_step": float(np.median(t)), "deposit_ms": float(np.median(dep)),
         "deposits_per_s": st["deposits"] / (float(np.median(t)) / 1e3),
+        "backward_ms": float(np.median(tb)),
         "slow_particle_tiles": st["slow_particle_tiles"]}
     model.close()
     return res

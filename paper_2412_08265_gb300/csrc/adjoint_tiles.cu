@@ -267,7 +267,11 @@ __device__ __noinline__ AdjSums adj_mean_general(const float4 w, const float4 g4
 }
 
 // Fast path of the bin means: the forward's 30-bin rounds (edge l on lane l;
-// see mean_rounds in deposit.cu) for the three interpolants at once.
+// see mean_rounds in deposit.cu), accumulated per corner as in adj_particle.
+// Lane l interpolates the four corner templates at its edge (L), takes the
+// next edge's (Ln) and the enclosed node's values, and adds G_j times twice
+// the corner's bin mean (U) and G_j times the corner's share of the v bracket
+// (T); the weights are applied once afterwards.
 template <int R>
 __device__ __forceinline__ AdjSums adj_mean_particle(const float4 w, const float4 g4, const TileCtx& C,
                                                      const float4* __restrict__ slab,
@@ -283,49 +287,66 @@ __device__ __forceinline__ AdjSums adj_mean_particle(const float4 w, const float
     if (!(delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R - 1) &&
           (unsigned)cr < (unsigned)C.ncb))
         return adj_mean_general<R>(w, g4, C, slab, quad, lane, grow, ls0_over);
-    const float s01 = w.x + w.y, s23 = w.z + w.w, s02 = w.x + w.z, s13 = w.y + w.w;
-    const float4 wa = make_float4(-s01, s01, -s23, s23), wb = make_float4(-s02, -s13, s02, s13);
     const float4* q = slab + (kw + lane) * C.ncb + cr;
     const int s30 = 30 * C.ncb, s29 = 29 * C.ncb;
     const float nld = -lanef * delta;
     const float d30 = 30.f * delta;
     const float A = 1.f - delta;
-    const float h = 0.5f / A, iA = 1.f / A;
-    float tb = ((float)K0 + lanef) + ls0_over;  // absolute node position of lane l's node, / dls
-    AdjSums S{0.f, 0.f, 0.f, 0.f};
+    const float iA = 1.f / A;
+    // absolute position of lane l's edge (node units + ls0/dls), 30 A further each round
+    float u = fmaf(lanef, A, ((float)K0 + f) + ls0_over);
+    const float du = 30.f * A;
+    const float2 mhalf = make_float2(-0.5f, -0.5f);
+    float2 U01 = make_float2(0.f, 0.f), U23 = U01, T01 = U01, T23 = U01;
 #pragma unroll
     for (int r = 0; r <= R; ++r) {
         float4 Q = make_float4(0.f, 0.f, 0.f, 0.f);
         if (r < R || lane <= R + 1) Q = *q;
-        const float M = quad_dot(w, Q), Ma = quad_dot(wa, Q), Mb = quad_dot(wb, Q);
         const float g = f + nld;
         const bool up = g >= 0.f;
         const int src = up ? lane + 1 : lane - 1;
-        const float XM = __shfl_sync(0xffffffffu, M, src);
-        const float XA = __shfl_sync(0xffffffffu, Ma, src);
-        const float XB = __shfl_sync(0xffffffffu, Mb, src);
+        const float2 Q01 = make_float2(Q.x, Q.y), Q23 = make_float2(Q.z, Q.w);
+        const float2 X01 = make_float2(__shfl_sync(0xffffffffu, Q.x, src), __shfl_sync(0xffffffffu, Q.y, src));
+        const float2 X23 = make_float2(__shfl_sync(0xffffffffu, Q.z, src), __shfl_sync(0xffffffffu, Q.w, src));
+        const float2 D01 = __fadd2_rn(X01, make_float2(-Q.x, -Q.y));
+        const float2 D23 = __fadd2_rn(X23, make_float2(-Q.z, -Q.w));
         const float ag = fabsf(g);
-        const float LM = fmaf(ag, XM - M, M), LA = fmaf(ag, XA - Ma, Ma), LB = fmaf(ag, XB - Mb, Mb);
-        const float LMn = __shfl_down_sync(0xffffffffu, LM, 1);
-        const float LAn = __shfl_down_sync(0xffffffffu, LA, 1);
-        const float LBn = __shfl_down_sync(0xffffffffu, LB, 1);
-        const float a = (up ? 1.f : 0.f) - g, b = A - a;
-        const float Sm = fmaf(0.5f, up ? XM : M, h * fmaf(a, LM, b * LMn));
-        const float Sa = fmaf(0.5f, up ? XA : Ma, h * fmaf(a, LA, b * LAn));
-        const float Sb = fmaf(0.5f, up ? XB : Mb, h * fmaf(a, LB, b * LBn));
+        const float2 L01 = __ffma2_rn(make_float2(ag, ag), D01, Q01);
+        const float2 L23 = __ffma2_rn(make_float2(ag, ag), D23, Q23);
+        const float2 N01 = make_float2(__shfl_down_sync(0xffffffffu, L01.x, 1), __shfl_down_sync(0xffffffffu, L01.y, 1));
+        const float2 N23 = make_float2(__shfl_down_sync(0xffffffffu, L23.x, 1), __shfl_down_sync(0xffffffffu, L23.y, 1));
+        // the node between the edges (the neighbour if g >= 0)
+        const float uf = up ? 1.f : 0.f;
+        const float2 K01 = __ffma2_rn(make_float2(uf, uf), D01, Q01);
+        const float2 K23 = __ffma2_rn(make_float2(uf, uf), D23, Q23);
+        const float ai = fmaf(-g, iA, up ? iA : 0.f);  // a / A
+        const float2 dd01 = __fadd2_rn(L01, make_float2(-N01.x, -N01.y));
+        const float2 dd23 = __fadd2_rn(L23, make_float2(-N23.x, -N23.y));
+        // twice the bin mean: M_K + L_{l+1} + (a/A)(L - L_{l+1})
+        const float2 v01 = __ffma2_rn(make_float2(ai, ai), dd01, __fadd2_rn(K01, N01));
+        const float2 v23 = __ffma2_rn(make_float2(ai, ai), dd23, __fadd2_rn(K23, N23));
         const float Gj = G[r];  // 0 for lanes that own no bin of the tile
-        S.sm = fmaf(Gj, Sm, S.sm);
-        S.sa = fmaf(Gj, Sa, S.sa);
-        S.sz = fmaf(Gj, Sb, S.sz);
-        S.sv = fmaf(Gj, fmaf((tb + g) * (LMn - LM), iA, LMn - Sm), S.sv);
+        const float2 G2 = make_float2(Gj, Gj);
+        U01 = __ffma2_rn(G2, v01, U01);
+        U23 = __ffma2_rn(G2, v23, U23);
+        // v bracket per corner: L_{l+1} - mean - u (L - L_{l+1}) / A
+        const float gu = -Gj * u * iA;
+        T01 = __ffma2_rn(G2, __ffma2_rn(mhalf, v01, N01), __ffma2_rn(make_float2(gu, gu), dd01, T01));
+        T23 = __ffma2_rn(G2, __ffma2_rn(mhalf, v23, N23), __ffma2_rn(make_float2(gu, gu), dd23, T23));
         if (r < R) {
             f -= d30;
             const bool carry = f < 0.f;
             f = carry ? f + 1.f : f;
             q += carry ? s29 : s30;
-            tb += carry ? 29.f : 30.f;
+            u += du;
         }
     }
+    const float s01 = w.x + w.y, s23 = w.z + w.w, s02 = w.x + w.z, s13 = w.y + w.w;
+    AdjSums S;
+    S.sm = 0.5f * fmaf(w.x, U01.x, fmaf(w.y, U01.y, fmaf(w.z, U23.x, w.w * U23.y)));
+    S.sa = 0.5f * fmaf(s01, U01.y - U01.x, s23 * (U23.y - U23.x));
+    S.sz = 0.5f * fmaf(s02, U23.x - U01.x, s13 * (U23.y - U01.y));
+    S.sv = fmaf(w.x, T01.x, fmaf(w.y, T01.y, fmaf(w.z, T23.x, w.w * T23.y)));
     return S;
 }
 
