@@ -182,7 +182,7 @@ def run_reference(args):
     from paper_2412_08265_gb300 import synth
     wl = synth.mid_galaxy(n=args.particles)
     times, deps = [], []
-    per_step = max(3.0, 60.0 / max(args.steps + args.warmup, 1))
+    per_step = args.ref_step_seconds or max(3.0, 60.0 / max(args.steps + args.warmup, 1))
     for i in range(args.warmup + args.steps):
         rate, cores, desc, _, _, dep, dt = oracle_sample(wl, per_step, seed=1000 + i)
         if i >= args.warmup:
@@ -657,6 +657,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=None,
+                    help="oracle work per step of --impl reference (default: about a minute in all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--particles", type=int, default=1_000_000,
                     help="particles of the mid-size galaxy (smaller only for profiler captures)")
