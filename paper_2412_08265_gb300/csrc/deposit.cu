@@ -35,8 +35,8 @@
 // the slab's halo, take a per-bin path.
 //
 // Spaxels with more than `chunk` particles are split into several items whose
-// FP32 partial rows K5 adds in FP64 in item order, so the cube is bitwise
-// reproducible and no global atomics are used.
+// FP32 partial rows K5 adds in item order (in FP64 for spaxels of many items),
+// so the cube is bitwise reproducible and no global atomics are used.
 #include "common.cuh"
 #include "kernels.h"
 #include "tile.cuh"
@@ -737,13 +737,25 @@ int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, 
 }
 
 // ----------------------------------------------------------------------------
-// K5: rows of split spaxels = FP64 sum of their partial rows in item order.
+// K5: rows of split spaxels = the sum of their partial rows in item order, in
+// FP64 for spaxels of more than kCombineF32Rows items (very high-count
+// spaxels), else in FP32.
 // ----------------------------------------------------------------------------
 __global__ void k_combine(const int* __restrict__ part_off, int n_s, int n_lambda, const float* __restrict__ partials,
                           float* __restrict__ cube, int pitch) {
     for (int s = blockIdx.x; s < n_s; s += gridDim.x) {
         const int p0 = part_off[s], p1 = part_off[s + 1];
         if (p1 <= p0) continue;
+        if (p1 - p0 <= kCombineF32Rows) {
+            // a few partial rows: FP32 adds lose nothing that the FP32 partial
+            // sums have not already lost, and the FP64 pipe is the slow one
+            for (int j = threadIdx.x; j < n_lambda; j += blockDim.x) {
+                float acc = 0.f;
+                for (int r = p0; r < p1; ++r) acc += partials[(long long)r * n_lambda + j];
+                cube[(long long)s * pitch + j] = acc;
+            }
+            continue;
+        }
         for (int j = threadIdx.x; j < n_lambda; j += blockDim.x) {
             double acc = 0.0;
             for (int r = p0; r < p1; ++r) acc += (double)partials[(long long)r * n_lambda + j];

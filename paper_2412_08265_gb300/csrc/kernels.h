@@ -173,7 +173,9 @@ int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, 
                    cudaStream_t st);
 size_t deposit_smem_bytes(int ncb, int slab_w);
 
-// K5: combine partial rows of split spaxels in FP64, fixed order.
+// K5: combine partial rows of split spaxels in a fixed order: FP32 for at most
+// kCombineF32Rows rows, FP64 above.
+constexpr int kCombineF32Rows = 4;
 int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube, int pitch,
                    cudaStream_t st);
 
