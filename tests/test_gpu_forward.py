@@ -272,11 +272,13 @@ def test_empty_outside_and_single(torch_cuda):
     model.close()
 
 
-def test_heavy_spaxel_split_fp64_combine(torch_cuda):
-    """> chunk particles in a single spaxel: split items combined in FP64."""
+@pytest.mark.parametrize("n", [600, 1024, 1025, 5000])
+def test_heavy_spaxel_split_combine(torch_cuda, n):
+    """More than one work item of particles in a single spaxel: the split items'
+    rows are combined in FP32 for up to 4 items (600, 1024 particles) and in
+    FP64 above (1025, 5000)."""
     wl = synth.small_galaxy()
     rng = np.random.default_rng(4)
-    n = 5000
     f = lambda a: np.asarray(a, dtype=np.float32)
     p = synth.Particles(x=f(rng.uniform(0.01, 0.49, n)), y=f(rng.uniform(0.01, 0.49, n)),
                         mass=f(np.exp(rng.normal(np.log(1e5), 0.5, n))),
