@@ -550,3 +550,36 @@ def test_mass_gradient_closed_form():
             continue
         s1 = brute.particle_spectrum(ssp, tel, 1.0, float(p.age[i]), float(p.Z[i]), float(p.v_los[i]))
         assert abs(dm[i] - (G.reshape(-1, tel.n_lambda)[k] * s1).sum()) < 1e-10 * np.abs(s1).sum()
+
+
+# --------------------------------------------------------------------------
+# seeded random configurations: the whole forward model against the brute force
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(12))
+def test_random_configurations_match_brute_force(seed):
+    """Random SSP grids, telescopes (bin width, redshift, flux scale, resampling
+    mode, PSF/LSF) and oriented 3-D or projected galaxies: the oracle's cube
+    against the independent brute force."""
+    rng = np.random.default_rng(1000 + seed)
+    n_age, n_Z = int(rng.integers(2, 6)), int(rng.integers(1, 5))
+    n_ls = int(rng.integers(40, 120))
+    ls_lo = float(rng.uniform(3900.0, 4100.0))
+    ssp = synth.ssp_grid(n_age, n_Z, n_ls, ls_lo, ls_lo + float(rng.uniform(1.0, 3.0)) * n_ls, seed=seed)
+    dls = ssp.dlambda
+    dl = float(dls * rng.uniform(0.4, 2.5))
+    n_l = int(rng.integers(8, 60))
+    tel = synth.Telescope(nx=int(rng.integers(2, 7)), ny=int(rng.integers(2, 7)),
+                          spaxel_size=float(rng.uniform(0.3, 1.2)), n_lambda=n_l,
+                          lambda0=float(ls_lo + rng.uniform(0.0, 0.5) * n_ls * dls), dlambda=dl,
+                          psf_fwhm=float(rng.choice([0.0, 1.3, 2.2])), lsf_sigma=float(rng.choice([0.0, 1.1 * dl])),
+                          z_cosmo=float(rng.choice([0.0, 0.002, 0.01])), flux_scale=float(rng.uniform(0.5, 2.0)),
+                          resample=int(rng.integers(0, 2)))
+    if seed % 2:
+        p = synth.disk_3d(30, seed, inclination=float(rng.uniform(0, np.pi)), r_scale=0.8,
+                          azimuth=float(rng.uniform(-np.pi, np.pi)), position_angle=float(rng.uniform(-np.pi, np.pi)))
+    else:
+        p = tiny_particles(n=30, seed=seed, spread=0.5 * tel.spaxel_size * max(tel.nx, tel.ny))
+    got = oracle.forward(p, ssp, tel, n_threads=2)
+    bf = brute.psf_lsf(brute.cube0(p, ssp, tel), tel)
+    scale = max(float(np.abs(bf).max()), 1e-300)
+    np.testing.assert_allclose(got, bf, rtol=0, atol=1e-10 * scale)
