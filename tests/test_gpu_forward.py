@@ -500,3 +500,40 @@ def test_bin_means_conserve_flux(torch_cuda):
     tot_g, tot_r = got.sum(axis=2), ref.sum(axis=2)
     assert float(np.abs(tot_g - tot_r).max()) <= 1e-5 * float(tot_r.max())
     model.close()
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_configurations(torch_cuda, seed):
+    """Seeded random SSP grids (sizes, wavelength steps), telescopes (field,
+    bin width and count, redshift, flux scale, resampling mode, PSF/LSF) and
+    galaxies (projected or 3-D with all three angles, velocity spread): the
+    GPU cube against the oracle. The random tilings reach other round counts,
+    age-band splits and both deposit paths."""
+    rng = np.random.default_rng(500 + seed)
+    n_ls = int(rng.integers(300, 2500))
+    ls_lo = float(rng.uniform(3800.0, 4200.0))
+    ssp = synth.ssp_grid(int(rng.integers(2, 30)), int(rng.integers(1, 8)), n_ls, ls_lo,
+                         ls_lo + float(rng.uniform(0.8, 2.5)) * n_ls, seed=seed)
+    dls = ssp.dlambda
+    dl = float(dls * rng.choice([rng.uniform(0.5, 0.97), rng.uniform(0.975, 1.0), rng.uniform(1.0, 2.5)]))
+    n_l = int(rng.integers(50, min(3000, int(0.8 * n_ls * dls / dl))))
+    tel = synth.Telescope(nx=int(rng.integers(3, 40)), ny=int(rng.integers(3, 40)),
+                          spaxel_size=float(rng.uniform(0.2, 1.0)), n_lambda=n_l,
+                          lambda0=float(ls_lo + 0.1 * n_ls * dls), dlambda=dl,
+                          psf_fwhm=float(rng.choice([0.0, 1.5, 2.5])), lsf_sigma=float(rng.choice([0.0, 1.2 * dl])),
+                          z_cosmo=float(rng.choice([0.0, 0.003])), flux_scale=float(rng.uniform(0.5, 2.0)),
+                          resample=int(rng.integers(0, 2)))
+    n = int(rng.integers(2_000, 30_000))
+    if seed % 2:
+        p = synth.disk_3d(n, 600 + seed, inclination=float(rng.uniform(0, np.pi)),
+                          azimuth=float(rng.uniform(-np.pi, np.pi)), position_angle=float(rng.uniform(-np.pi, np.pi)),
+                          sigma_v=float(rng.uniform(20, 300)))
+    else:
+        p = synth.disk_projected(n, 600 + seed, sigma_v=float(rng.uniform(20, 300)))
+    model = make_model(ssp, tel, n=p.n)
+    got = model.forward(p).cpu().numpy()
+    ref = oracle.forward(p, ssp, tel, n_threads=NT)
+    assert np.abs(ref).max() > 0
+    assert rel_err(got, ref) <= TOL_F32, (seed, tel)
+    assert model.stats()["device_error"] == 0
+    model.close()
