@@ -177,3 +177,33 @@ def test_backward_oriented_3d_and_angle_gradients(torch_cuda, resample):
         exp = float((odv * d).sum())
         assert abs(glob[c] - exp) <= 1e-4 * float(np.abs(odv * d).sum()), (c, glob[c], exp)
         assert abs(exp) > 0.0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_backward_random_configurations(torch_cuda, seed):
+    """Seeded random grids, telescopes (bin width, redshift, flux scale,
+    resampling mode, PSF/LSF) and projected or oriented 3-D galaxies: the
+    adjoint against the oracle's gradient for a random cotangent."""
+    rng = np.random.default_rng(700 + seed)
+    n_ls = int(rng.integers(300, 2000))
+    ls_lo = float(rng.uniform(3800.0, 4200.0))
+    ssp = synth.ssp_grid(int(rng.integers(2, 20)), int(rng.integers(1, 6)), n_ls, ls_lo,
+                         ls_lo + float(rng.uniform(0.8, 2.5)) * n_ls, seed=seed)
+    dls = ssp.dlambda
+    dl = float(dls * rng.choice([rng.uniform(0.5, 0.97), rng.uniform(0.975, 1.0), rng.uniform(1.0, 2.5)]))
+    n_l = int(rng.integers(50, min(1500, int(0.8 * n_ls * dls / dl))))
+    tel = synth.Telescope(nx=int(rng.integers(3, 24)), ny=int(rng.integers(3, 24)),
+                          spaxel_size=float(rng.uniform(0.3, 1.0)), n_lambda=n_l,
+                          lambda0=float(ls_lo + 0.1 * n_ls * dls), dlambda=dl,
+                          psf_fwhm=float(rng.choice([0.0, 1.5])), lsf_sigma=float(rng.choice([0.0, 1.2 * dl])),
+                          z_cosmo=float(rng.choice([0.0, 0.003])), flux_scale=float(rng.uniform(0.5, 2.0)),
+                          resample=int(rng.integers(0, 2)))
+    n = int(rng.integers(2_000, 12_000))
+    if seed % 2:
+        p = synth.disk_3d(n, 800 + seed, inclination=float(rng.uniform(0, np.pi)),
+                          azimuth=float(rng.uniform(-np.pi, np.pi)), position_angle=float(rng.uniform(-np.pi, np.pi)))
+    else:
+        p = synth.disk_projected(n, 800 + seed)
+    wl = synth.Workload("random", p, ssp, tel)
+    G = rng.standard_normal((tel.ny, tel.nx, tel.n_lambda))
+    _grad_check(torch_cuda, wl, G)
