@@ -285,7 +285,7 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     A.dv_dang = P.d_dvda;
     A.n_in = P.last_n;  // upper bound; the kernel reads the in-field count on the device
 #ifdef RUBIX_ADJ_WARP
-    if (P.tel.resample) return fail(RUBIX_ERR_INVALID_ARG, "this build's backward supports resample = 0 only");
+    if (P.tel.resample) return fail(RUBIX_ERR_INVALID_ARG, "the one-warp-per-particle adjoint supports resample = 0 only");
     launch_adjoint_rec(A, P.d_rec, st);  // one warp per particle over every bin
 #else
     // over the deposit's (tile, work item, age band) decomposition and slabs
