@@ -59,3 +59,34 @@ def test_invalid_arguments_are_reported_without_a_gpu(lib_path):
     assert rc == capi.RUBIX_ERR_INVALID_ARG and h.value is None
     assert b"NULL" in capi.load().rubix_last_error_message()
 
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of rubix_ssp_grid, rubix_telescope and rubix_particles
+    have the size and field offsets the C compiler gives the header's structs."""
+    import ctypes
+    import subprocess
+    from paper_2412_08265_gb300 import capi
+    structs = {"rubix_ssp_grid": capi.rubix_ssp_grid, "rubix_telescope": capi.rubix_telescope,
+               "rubix_particles": capi.rubix_particles}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rubix.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.check_call(["gcc", "-I", os.path.join(root, "include"), "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {}
+    for l in out:
+        if l:
+            parts = l.split()
+            got[tuple(parts[:-1])] = int(parts[-1])
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
