@@ -259,9 +259,12 @@ def rubix_selftest_bounded_wait(limit_s: float) -> bool:
     return bool(t.value)
 
 
-def last_error_message() -> str:
+def rubix_last_error_message() -> str:
     m = load().rubix_last_error_message()
     return m.decode() if m else ""
+
+
+last_error_message = rubix_last_error_message
 
 
 def rubix_version() -> str:

@@ -90,3 +90,14 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_every_entry_point_has_a_binding():
+    """The Python binding exposes every function the header declares, by name."""
+    from paper_2412_08265_gb300 import capi
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "include", "rubix.h")) as f:
+        names = set(re.findall(r"\b(rubix_[a-z0-9_]+)\s*\(", f.read()))
+    assert names
+    missing = [n for n in sorted(names) if not hasattr(capi, n)]
+    assert not missing, missing
