@@ -101,3 +101,19 @@ def test_every_entry_point_has_a_binding():
     assert names
     missing = [n for n in sorted(names) if not hasattr(capi, n)]
     assert not missing, missing
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the CUDA library the binding raises; there is no CPU fallback."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2412_08265_gb300 import capi\n"
+            "capi.LIB_PATH = %r\n"
+            "try:\n"
+            "    capi.rubix_version()\n"
+            "except RuntimeError as e:\n"
+            "    print('RAISED', e)\n") % (root, str(tmp_path / "absent" / "librubix.so"))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert "RAISED CUDA library not built" in out.stdout, out.stdout + out.stderr
