@@ -152,8 +152,18 @@ rubix_status rubix_cube_forward(rubix_cube_t *h, const rubix_particles *p, uint6
                                 float noise_s2n, float *cube_out, int32_t cube_on_device,
                                 void *stream);
 
+/* Tag of the most recent successful rubix_cube_forward on this handle: 1 for
+ * the first forward, one more for each later one (0 before any). The
+ * backward state a handle keeps (sorted particles, per-particle setup)
+ * belongs to that forward only; rubix_cube_backward checks the tag. */
+rubix_status rubix_cube_forward_tag(rubix_cube_t *h, uint64_t *tag);
+
 /* Adjoint of the most recent noiseless forward on this handle (gradients
- * through the pipeline, Abstract / Sec. 1). dL_dcube: device pointer, float32
+ * through the pipeline, Abstract / Sec. 1). forward_tag must be that
+ * forward's tag (rubix_cube_forward_tag, read after the forward): a backward
+ * meant for an earlier forward -- whose particles the handle no longer holds
+ * -- is refused with INVALID_ARG instead of differentiating the wrong
+ * particles. dL_dcube: device pointer, float32
  * [ny][nx][n_lambda]. Outputs (device pointers, float32 [n], original particle
  * order, any may be NULL): dL/dmass, dL/dage (per Gyr), dL/dZ, dL/dv_los
  * (per km/s). Out-of-field particles get 0. d_global (device, nullable,
@@ -164,10 +174,11 @@ rubix_status rubix_cube_forward(rubix_cube_t *h, const rubix_particles *p, uint6
  * likewise (positions carry no gradient, so the position angle has none and
  * preprojected input gives 0 for [2] and [3]); each summed in FP64 in a fixed
  * order.
- * Errors: INVALID_ARG (no forward yet, or the forward used noise), CUDA. */
-rubix_status rubix_cube_backward(rubix_cube_t *h, const float *dL_dcube, float *d_mass,
-                                 float *d_age, float *d_Z, float *d_vlos, double *d_global,
-                                 void *stream);
+ * Errors: INVALID_ARG (no forward yet, a tag other than the most recent
+ * forward's, or the forward used noise), CUDA. */
+rubix_status rubix_cube_backward(rubix_cube_t *h, uint64_t forward_tag, const float *dL_dcube,
+                                 float *d_mass, float *d_age, float *d_Z, float *d_vlos,
+                                 double *d_global, void *stream);
 
 rubix_status rubix_cube_destroy(rubix_cube_t *h);
 
@@ -232,7 +243,7 @@ rubix_status rubix_spaxel_sort_noalloc(const rubix_particles *p, const rubix_tel
  * Serving: many galaxies through one resident SSP grid.
  *
  * The paper motivates fast forward modelling for large simulation suites and
- * inference loops (Sec. 1, Sec. 6) but defines no server; this is the
+ * inference loops (Sec. 1, Sec. 5) but defines no server; this is the
  * library's request interface for that use. A server owns one device copy of
  * the SSP grid, tiled for one output wavelength grid, and a host thread that
  * runs a continuous-batching loop:

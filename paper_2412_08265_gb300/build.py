@@ -18,8 +18,11 @@ LIB = os.path.join(LIBDIR, "librubix.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "engine.cu", "serve.cu", "sort.cu", "deposit.cu", "psf_lsf.cu", "adjoint.cu", "adjoint_tiles.cu", "noalloc.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I", INCLUDE, "-I", CSRC]
+# Host code is compiled without floating-point contraction: the orientation
+# matrix and the key coordinates are defined with every product and sum
+# rounded once (no fused multiply-add), on x86 and Arm hosts alike.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 
 def _nvcc() -> str:

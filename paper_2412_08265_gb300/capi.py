@@ -71,8 +71,9 @@ _SIGS = {
                                       C.POINTER(C.c_void_p)]),
     "rubix_cube_forward": (C.c_int32, [C.c_void_p, C.POINTER(rubix_particles), C.c_uint64, C.c_float,
                                        C.c_void_p, C.c_int32, C.c_void_p]),
-    "rubix_cube_backward": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                        C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rubix_cube_forward_tag": (C.c_int32, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "rubix_cube_backward": (C.c_int32, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rubix_cube_destroy": (C.c_int32, [C.c_void_p]),
     "rubix_cube_spaxel_keys": (C.c_int32, [C.c_void_p, C.POINTER(rubix_particles), C.c_void_p, C.c_void_p]),
     "rubix_cube_sorted": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -147,10 +148,16 @@ def rubix_cube_forward(h: int, p: rubix_particles, noise_seed: int, noise_s2n: f
           C.c_void_p(cube_out), C.c_int32(cube_on_device), C.c_void_p(stream))
 
 
-def rubix_cube_backward(h: int, dL_dcube: int, d_mass: int, d_age: int, d_Z: int, d_vlos: int,
-                        d_global: int, stream: int) -> None:
-    _call("rubix_cube_backward", C.c_void_p(h), C.c_void_p(dL_dcube), C.c_void_p(d_mass),
-          C.c_void_p(d_age), C.c_void_p(d_Z), C.c_void_p(d_vlos), C.c_void_p(d_global),
+def rubix_cube_forward_tag(h: int) -> int:
+    t = C.c_uint64()
+    _call("rubix_cube_forward_tag", C.c_void_p(h), C.byref(t))
+    return int(t.value)
+
+
+def rubix_cube_backward(h: int, forward_tag: int, dL_dcube: int, d_mass: int, d_age: int, d_Z: int,
+                        d_vlos: int, d_global: int, stream: int) -> None:
+    _call("rubix_cube_backward", C.c_void_p(h), C.c_uint64(forward_tag), C.c_void_p(dL_dcube),
+          C.c_void_p(d_mass), C.c_void_p(d_age), C.c_void_p(d_Z), C.c_void_p(d_vlos), C.c_void_p(d_global),
           C.c_void_p(stream))
 
 

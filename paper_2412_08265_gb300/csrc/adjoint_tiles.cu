@@ -46,7 +46,7 @@ __global__ void k_adj_setup(const AdjointParams P, const DepRec* __restrict__ re
 int launch_adjoint_setup(const AdjointParams& P, const DepRec* rec, float4* wu, cudaStream_t st) {
     if (P.n_in <= 0) return 0;
     long long nb = (P.n_in + 255) / 256;
-    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb > 16ll * sm_count()) nb = 16ll * sm_count();
     k_adj_setup<<<(int)nb, 256, 0, st>>>(P, rec, wu);
     return 1;
 }
@@ -567,7 +567,7 @@ __global__ void k_adj_final(const AdjointParams P, const float4* __restrict__ pa
 int launch_adjoint_final(const AdjointParams& P, const float4* part, int n_tiles, long long n_cap, cudaStream_t st) {
     if (P.n_in <= 0) return 0;
     long long nb = (P.n_in + 255) / 256;
-    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb > 16ll * sm_count()) nb = 16ll * sm_count();
     k_adj_final<<<(int)nb, 256, 0, st>>>(P, part, n_tiles, n_cap);
     return 1;
 }

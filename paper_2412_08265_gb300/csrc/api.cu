@@ -126,6 +126,7 @@ extern "C" rubix_status rubix_cube_forward(rubix_cube_t* h, const rubix_particle
     CK(cudaGetLastError());
     P.have_forward = true;
     P.forward_noise = noise;
+    P.forward_tag += 1;
     if (!cube_on_device) {
         CK(cudaMemcpyAsync(cube_out, out, cube_n * 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -244,12 +245,24 @@ extern "C" rubix_status rubix_cube_stats(rubix_cube_t* h, int64_t* stats, int32_
 // ----------------------------------------------------------------------------
 // backward
 // ----------------------------------------------------------------------------
-extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcube, float* d_mass, float* d_age,
-                                            float* d_Z, float* d_vlos, double* d_global, void* stream) {
+extern "C" rubix_status rubix_cube_forward_tag(rubix_cube_t* h, uint64_t* tag) {
+    if (!h || !tag) return fail(RUBIX_ERR_INVALID_ARG, "NULL argument");
+    *tag = h->P.have_forward ? h->P.forward_tag : 0;
+    return RUBIX_OK;
+}
+
+extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, uint64_t forward_tag, const float* dL_dcube,
+                                            float* d_mass, float* d_age, float* d_Z, float* d_vlos,
+                                            double* d_global, void* stream) {
     if (!h || !dL_dcube) return fail(RUBIX_ERR_INVALID_ARG, "NULL argument");
     const SspState& S = *h->S;
     Plan& P = h->P;
     if (!P.have_forward) return fail(RUBIX_ERR_INVALID_ARG, "backward needs a forward on this handle first");
+    if (forward_tag != P.forward_tag)
+        return fail(RUBIX_ERR_INVALID_ARG,
+                    "backward for forward %llu, but the handle holds the state of forward %llu (a later forward "
+                    "replaced it)",
+                    (unsigned long long)forward_tag, (unsigned long long)P.forward_tag);
     if (P.forward_noise) return fail(RUBIX_ERR_INVALID_ARG, "backward of a noisy forward is not defined");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(S.device));
@@ -284,10 +297,6 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     A.contrib = d_global ? P.d_contrib : nullptr;
     A.dv_dang = P.d_dvda;
     A.n_in = P.last_n;  // upper bound; the kernel reads the in-field count on the device
-#ifdef RUBIX_ADJ_WARP
-    if (P.tel.resample) return fail(RUBIX_ERR_INVALID_ARG, "the one-warp-per-particle adjoint supports resample = 0 only");
-    launch_adjoint_rec(A, P.d_rec, st);  // one warp per particle over every bin
-#else
     // over the deposit's (tile, work item, age band) decomposition and slabs
     launch_adjoint_setup(A, P.d_rec, P.d_wu, st);
     AdjTileParams T{};
@@ -320,7 +329,6 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, const float* dL_dcu
     if (launch_adjoint_tiles(T, &S.tmap, S.dep_ctas, S.dep_threads, S.dep_smem, st) < 0)
         return fail(RUBIX_ERR_CUDA, "adjoint launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     launch_adjoint_final(A, P.d_adjpart, S.n_tiles, P.cap, st);
-#endif
     if (d_global)
         launch_reduce_global(P.d_contrib, P.d_seg_off + (size_t)P.n_s * S.n_bands, d_global, P.d_red, st);
     CK(cudaGetLastError());

@@ -96,6 +96,24 @@ cudaError_t dalloc_sync(T** p, size_t count) {
 
 }  // namespace
 
+int sm_count() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev >= 64) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 1;
+    }
+    int n = __atomic_load_n(&cache[dev], __ATOMIC_RELAXED);
+    if (n <= 0) {
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+        __atomic_store_n(&cache[dev], n, __ATOMIC_RELAXED);
+    }
+    return n;
+}
+
 // ----------------------------------------------------------------------------
 // validation
 // ----------------------------------------------------------------------------

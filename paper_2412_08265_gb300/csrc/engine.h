@@ -104,6 +104,7 @@ struct Plan {
     size_t bytes = 0;                       // device bytes held by the plan
     // state of the last forward
     bool have_forward = false, forward_noise = false;
+    uint64_t forward_tag = 0;               // tag of the last forward (1, 2, ...)
     long long last_n = 0;
     int launches = 0, dep_launches = 0;
 };

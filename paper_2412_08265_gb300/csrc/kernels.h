@@ -14,6 +14,10 @@ struct Item;
 
 constexpr int kMaxBands = 32;
 
+// Streaming multiprocessors of the current device (cached per device); grid
+// caps of the grid-stride kernels are multiples of it.
+int sm_count();
+
 // Deposit launch shape: threads per CTA (one CTA per SM: the SSP slab fills
 // shared memory; 896 threads leave 72 registers per thread).
 #ifndef RUBIX_DEP_THREADS
@@ -217,7 +221,6 @@ struct AdjointParams {
     const float2* dv_dang;     // [n] original order: dv_los/d(inclination), dv_los/d(azimuth)
     long long n_in;            // upper bound (grid sizing)
 };
-int launch_adjoint_rec(const AdjointParams& P, const DepRec* rec, cudaStream_t st);
 
 // Adjoint over the deposit's (wavelength tile, work item, age band)
 // decomposition: per (tile, particle) the four sums

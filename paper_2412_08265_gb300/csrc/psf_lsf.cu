@@ -253,9 +253,6 @@ static bool launch_fused(const ConvParams& P, const float* in, float* out, cudaS
 #define RUBIX_FUSED_RADII(X) X(3, 4) X(3, 2) X(3, 0) X(0, 4) X(0, 2) X(2, 4) X(4, 4) X(3, 3) X(3, 5)
 
 static bool try_fused(const ConvParams& P, const float* in, float* out, cudaStream_t st) {
-#ifdef RUBIX_PSF_TWO_PASS
-    return false;
-#endif
 #define RUBIX_FUSED_CASE(RP_, RL_) \
     if (P.rp == RP_ && P.rl == RL_) return launch_fused<RP_, RL_>(P, in, out, st);
     RUBIX_FUSED_RADII(RUBIX_FUSED_CASE)
@@ -457,9 +454,6 @@ static bool try_tma(const ConvParams& P, const CUtensorMap* map, float* out, cud
 }
 
 bool psf_lsf_needs_tmp(int rp, int rl) {
-#ifdef RUBIX_PSF_TWO_PASS
-    return true;
-#endif
 #define RUBIX_FUSED_HAS(RP_, RL_) \
     if (rp == RP_ && rl == RL_) return false;
     RUBIX_FUSED_RADII(RUBIX_FUSED_HAS)

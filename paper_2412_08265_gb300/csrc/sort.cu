@@ -8,10 +8,14 @@
 namespace rubix {
 
 // ----------------------------------------------------------------------------
-// K1: orientation + spaxel key. Reading: x' = x, y' = y cos i - z sin i,
-// v = vy sin i + vz cos i; x_lo = (-0.5 nx) size; u = (x' - x_lo) * (1/size);
-// every FP64 op rounded once (explicit _rn intrinsics, no contraction), so the
-// integer key is bit-identical to a host evaluation of the same expression.
+// K1: orientation + spaxel key. Reading: with the orientation matrix R built
+// on the host (R = Rz(position angle) Rx(inclination) Rz(azimuth), its
+// elements rounded as the ABI header states, no contraction),
+// x' = (R00 x + R01 y) + R02 z, y' likewise, v_los = (R20 vx + R21 vy) + R22 vz;
+// x_lo = (-0.5 nx) size; u = (x' - x_lo) * (1/size); every FP64 op rounded
+// once (explicit _rn intrinsics), so the integer key is bit-identical to a
+// host evaluation of the same expression. Pre-projected input takes (x', y',
+// v_los) as given.
 // With age bands the sort key appends the particle's band (an internal
 // partition of the SSP grid used by the deposit) below the spaxel index.
 // ----------------------------------------------------------------------------
@@ -290,7 +294,7 @@ int launch_sort_by_key(const int* keys, long long n, int n_keys, int* keys_tmp, 
 int launch_assign(const AssignParams& P, cudaStream_t st) {
     if (P.n <= 0) return 0;
     long long nb = (P.n + 255) / 256;
-    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb > 16ll * sm_count()) nb = 16ll * sm_count();
     k_assign<<<(int)nb, 256, 0, st>>>(P);
     return 1;
 }

@@ -44,6 +44,7 @@ class CubeModel:
         with torch.cuda.device(self.device):
             self.handle = capi.rubix_cube_create(g, t, int(max_particles))
         self._last = None
+        self.last_tag = 0
 
     @staticmethod
     def c_telescope(tel) -> capi.rubix_telescope:
@@ -108,16 +109,21 @@ class CubeModel:
         capi.rubix_cube_forward(self.handle, cp, int(noise_seed), float(noise_s2n), out.data_ptr(), 1,
                                 st.cuda_stream)
         self._last = d  # keep the device arrays alive until the kernels have read them
+        self.last_tag = capi.rubix_cube_forward_tag(self.handle)
         return out
 
     def backward(self, dL_dcube: torch.Tensor, want_global: bool = False,
-                 stream: torch.cuda.Stream | None = None):
+                 stream: torch.cuda.Stream | None = None, forward_tag: int | None = None):
+        """Gradients of the forward with tag `forward_tag` (default: the most
+        recent forward); raises RubixError if a later forward has replaced
+        that forward's state on the handle."""
         n = int(self._last["mass"].shape[0])
+        tag = self.last_tag if forward_tag is None else int(forward_tag)
         g = [torch.empty(n, dtype=torch.float32, device=self.device) for _ in range(4)]
         glob = torch.empty(4, dtype=torch.float64, device=self.device) if want_global else None
         st = stream or torch.cuda.current_stream(self.device)
         dc = dL_dcube.to(torch.float32).contiguous()
-        capi.rubix_cube_backward(self.handle, dc.data_ptr(), g[0].data_ptr(), g[1].data_ptr(),
+        capi.rubix_cube_backward(self.handle, tag, dc.data_ptr(), g[0].data_ptr(), g[1].data_ptr(),
                                  g[2].data_ptr(), g[3].data_ptr(), glob.data_ptr() if glob is not None else 0,
                                  st.cuda_stream)
         return (*g, glob)
@@ -172,9 +178,13 @@ class RubixCube(torch.autograd.Function):
              "v_los": v_los.detach().contiguous(), "preprojected": True, "inclination": 0.0}
         cube = model.forward(d)
         ctx.model = model
+        ctx.forward_tag = model.last_tag
         return cube
 
     @staticmethod
     def backward(ctx, grad_cube):
-        dm, da, dz, dv, _ = ctx.model.backward(grad_cube)
+        # the handle keeps the state of its most recent forward only: a graph
+        # holding two applications of one model can differentiate the last
+        # one, and the library refuses the earlier one (RubixError)
+        dm, da, dz, dv, _ = ctx.model.backward(grad_cube, forward_tag=ctx.forward_tag)
         return dm, da, dz, dv, None, None, None

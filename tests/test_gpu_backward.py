@@ -120,6 +120,37 @@ def test_autograd_function(torch_cuda):
     model.close()
 
 
+def test_backward_refuses_a_replaced_forward(torch_cuda):
+    """A handle keeps the state of its most recent forward only. Two
+    RubixCube.apply calls on one model in one graph: loss.backward() reaches
+    the later application first (its gradient is right), then the earlier
+    one, whose forward state has been replaced -- the library refuses it
+    (forward tag mismatch) instead of returning the later galaxy's gradients."""
+    torch = torch_cuda
+    from paper_2412_08265_gb300 import capi
+    from paper_2412_08265_gb300.model import CubeModel, RubixCube
+    wl = synth.small_galaxy(n=2000, seed=3)
+    p = wl.particles
+    model = CubeModel(wl.ssp, wl.telescope, "f32", max_particles=p.n)
+    t = lambda a, g=False: torch.tensor(a, device="cuda", requires_grad=g)
+    mass, age, Z, v = t(p.mass, True), t(p.age, True), t(p.Z, True), t(p.v_los, True)
+    c1 = RubixCube.apply(mass, age, Z, v, t(p.x), t(p.y), model)
+    assert model.last_tag == 1
+    c2 = RubixCube.apply(mass * 2.0, age, Z, v, t(p.x), t(p.y), model)
+    assert model.last_tag == 2
+    loss = c1.sum() + c2.sum()
+    with pytest.raises(capi.RubixError, match="later forward replaced it"):
+        loss.backward()
+    # through the ABI: the earlier tag is refused, the current one accepted
+    g = torch.ones(model.cube_shape, device="cuda")
+    with pytest.raises(capi.RubixError):
+        model.backward(g, forward_tag=1)
+    dm, _, _, _, _ = model.backward(g, forward_tag=2)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(dm).all())
+    model.close()
+
+
 @pytest.mark.parametrize("z", [0.005, 0.02])
 def test_backward_redshifted_and_scaled(torch_cuda, z):
     """Galaxy at redshift z with a flux scale: z = 0.005 keeps the deposit's

@@ -100,6 +100,30 @@ def test_spaxel_keys_bit_exact(torch_cuda, kind):
     model.close()
 
 
+@pytest.mark.parametrize("angles", [(0.83, 0.0, 0.61), (1.3, -2.4, 0.61), (0.3, 1.1, -1.2), (1.2, 0.4, 2.5)])
+def test_keys_within_ulps_of_edges_bit_exact(torch_cuda, angles):
+    """3-D particles whose rotated x' or y' lies within 3 FP64 ulps of a
+    spaxel edge (tests/_edges.py; a one-ulp change of the rotation matrix
+    moves hundreds of them, pinned on the CPU): the GPU keys, with the matrix
+    built by the library's host code, equal the oracle's bit for bit."""
+    import _edges as edges
+    tel = synth.serving_telescope(73)
+    i, a, q = angles
+    x, y, z = edges.near_edge_particles(tel, i, a, q, n_edges=64, seed=1)
+    n = len(x)
+    zero = np.zeros(n, np.float32)
+    p = synth.Particles(x=x, y=y, z=z, vx=zero, vy=zero, vz=zero, mass=np.full(n, 1e5, np.float32),
+                        age=np.ones(n, np.float32), Z=np.full(n, 0.01, np.float32), preprojected=False,
+                        inclination=i, azimuth=a, position_angle=q)
+    wl = synth.small_galaxy()
+    model = make_model(wl.ssp, tel, n=n)
+    got = model.spaxel_keys(p).cpu().numpy()
+    xp, yp, _ = oracle.orient(p)
+    ref = oracle.spaxel_keys(xp, yp, tel)
+    assert np.array_equal(got, ref), np.flatnonzero(got != ref)[:10]
+    model.close()
+
+
 def test_sort_and_segments_bit_exact(torch_cuda):
     wl = synth.mid_galaxy(n=300_000)
     model = make_model(wl, n=wl.particles.n)

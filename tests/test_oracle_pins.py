@@ -155,6 +155,42 @@ def test_spaxel_keys_vs_exact_rationals():
     assert n_checked > 1500
 
 
+NEAR_EDGE_ANGLES = [(0.83, 0.0, 0.61), (1.3, -2.4, 0.61), (0.3, 1.1, -1.2), (1.2, 0.4, 2.5)]
+
+
+@pytest.mark.parametrize("angles", NEAR_EDGE_ANGLES)
+def test_near_edge_particles_resolve_one_ulp_of_the_rotation(angles):
+    """The near-edge inputs of the GPU key test (tests/_edges.py): the test's
+    own projection is the oracle's bit for bit, every constructed x' or y'
+    lies within 3 FP64 ulps of a key edge, and a one-ulp change of any
+    in-plane element of R (R00, R01, R10, R11) moves some of them to another
+    spaxel -- so a GPU host that rounds R differently cannot pass."""
+    import _edges as edges
+    tel = synth.serving_telescope(73)
+    i, a, q = angles
+    x, y, z = edges.near_edge_particles(tel, i, a, q, n_edges=64, seed=1)
+    n = len(x)
+    assert n > 1000
+    zero = np.zeros(n, np.float32)
+    p = synth.Particles(x=x, y=y, z=z, vx=zero, vy=zero, vz=zero, mass=np.full(n, 1e5, np.float32),
+                        age=np.ones(n, np.float32), Z=np.full(n, 0.01, np.float32), preprojected=False,
+                        inclination=i, azimuth=a, position_angle=q)
+    xp, yp, _ = oracle.orient(p)
+    R = edges.rotation(i, a, q)
+    ex, ey = edges.project(R, x, y, z)
+    assert np.array_equal(xp, ex) and np.array_equal(yp, ey)
+    key = oracle.spaxel_keys(xp, yp, tel)
+    assert np.array_equal(key, edges.keys(ex, ey, tel))
+    size = tel.spaxel_size
+    d = [np.abs(c - (lo + np.round((c - lo) / size) * size)) for c, lo in
+         ((xp, (-0.5 * tel.nx) * size), (yp, (-0.5 * tel.ny) * size))]
+    assert float(np.minimum(d[0], d[1]).max()) < 1e-14
+    for idx in (0, 1, 3, 4):
+        for direction in (math.inf, -math.inf):
+            px, py = edges.project(edges.perturbed(R, idx, direction), x, y, z)
+            assert (edges.keys(px, py, tel) != key).sum() > 0, (idx, direction)
+
+
 def test_stable_sort_matches_numpy_stable_argsort():
     rng = np.random.default_rng(0)
     key = rng.integers(0, 37, 5000).astype(np.int32)
