@@ -1,12 +1,15 @@
 """Benchmark of the particle -> IFU cube forward model on GB300.
 
-One step = one full forward (orient + spaxel keys, sort, SSP lookup + Doppler
-resampling + per-spaxel deposit, FP64 combine, PSF + LSF) of the mid-size
-galaxy workload: 1e6 star particles (exponential disk), SSP grid 50 ages x 10
-metallicities x 3721 wavelengths in FP32, IFU of 150 x 150 spaxels of 0.2 kpc
-x 3721 bins of 1.25 A from 4750 A, Gaussian PSF (FWHM 1.5 spaxels) and LSF
-(sigma 1.2 A). Metric: particle-wavelength deposits per second (in-field
-particles x wavelength bins / step time), with p50/p99 cube latency.
+One step = one full forward (spaxel keys, sort, SSP lookup + Doppler
+resampling + per-spaxel deposit, combine of split spaxels, PSF + LSF) of the
+large galaxy workload: 2e7 star particles (30% Hernquist bulge + exponential
+disk), SSP grid 50 ages x 10 metallicities x 3721 wavelengths stored in BF16
+(FP32 arithmetic), IFU of 300 x 300 spaxels of 0.1 kpc x 3721 bins of 1.25 A
+from 4750 A, Gaussian PSF (FWHM 1.5 spaxels) and LSF (sigma 1.2 A) -- the
+largest single-GPU configuration. Metric: particle-wavelength deposits per
+second (in-field particles x wavelength bins / step time), with p50/p99 cube
+latency. The mid-size galaxy (1e6 particles, FP32 templates), the
+differentiable step, bin means and the serving stream are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -16,6 +19,7 @@ Under torchrun each rank forward-models its own galaxy on its own GPU
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -32,11 +36,53 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-wavelength deposits/s and p50/p99 cube latency at stated rel err"
 UNIT = "deposits/s"
 FLOPS_PER_DEPOSIT = 16  # 4 SSP corners x 2 wavelength neighbours, one FMA each
-REL_ERR_BOUND = 1e-5
-# DRAM bytes (read + write) per deposit launch on the mid-size workload (1e6
-# particles), from the ncu capture summarised in profiles/k_deposit_mid-disk-1e6p.md;
-# None when the kernel or the workload differs from that capture.
-DEPOSIT_TRAFFIC_BYTES = 2.515222e9 + 2.767698e9
+REL_ERR_BOUND = {"f32": 1e-5, "bf16": 2e-3}
+CSRC = os.path.join(ROOT, "paper_2412_08265_gb300", "csrc")
+# sources of the deposit kernel's code: a recorded DRAM traffic figure holds
+# only for the kernel built from the same sources
+DEPOSIT_SOURCES = ("deposit.cu", "tile.cuh", "common.cuh")
+
+
+def deposit_sources_sha() -> str:
+    h = hashlib.sha256()
+    for name in DEPOSIT_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes (read + write) of one deposit launch of `workload`, from the
+    ncu summary profiles/k_deposit_<workload>.md (its lines
+    `dram_bytes_per_launch: <bytes>` and `deposit_sources_sha256: <hash>`),
+    or None if there is none or it was taken from other kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"k_deposit_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    vals = {}
+    for line in text.splitlines():
+        line = line.strip().strip("`")
+        for key in ("dram_bytes_per_launch", "deposit_sources_sha256"):
+            if line.startswith(key + ":"):
+                vals[key] = line.split(":", 1)[1].strip()
+    if vals.get("deposit_sources_sha256") != deposit_sources_sha() or "dram_bytes_per_launch" not in vals:
+        return None, os.path.relpath(path, ROOT)
+    return float(vals["dram_bytes_per_launch"]), os.path.relpath(path, ROOT)
+
+
+def measured_fp32_peak():
+    """FP32 FMA peak measured on this device now (FFMA and packed FFMA2 chain
+    benchmarks in the library; the larger is the denominator)."""
+    from paper_2412_08265_gb300 import capi
+    runs = []
+    for packed in (False, True):
+        f, per_clk, mhz = capi.rubix_measure_fp32_peak(packed)
+        runs.append({"kind": "FFMA2" if packed else "FFMA", "tflops": f / 1e12, "fma_per_clk_per_sm": per_clk,
+                     "sm_mhz": mhz})
+    best = max(runs, key=lambda r: r["tflops"])
+    return best, runs
 
 
 def dist_env():
@@ -180,7 +226,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2412_08265_gb300 import synth
-    wl = synth.mid_galaxy(n=args.particles)
+    wl = synth.large_galaxy() if args.workload == "large" else synth.mid_galaxy(n=args.particles)
     times, deps = [], []
     per_step = args.ref_step_seconds or max(3.0, 60.0 / max(args.steps + args.warmup, 1))
     for i in range(args.warmup + args.steps):
@@ -193,8 +239,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": wl.name, "n_particles": wl.particles.n, "spaxels": "150x150",
-                       "n_lambda": 3721, "ssp": "50x10x3721", "sample": "bounded spaxel subset per step"},
+            "config": {"workload": wl.name, "n_particles": wl.particles.n,
+                       "spaxels": f"{wl.telescope.nx}x{wl.telescope.ny}", "n_lambda": wl.telescope.n_lambda,
+                       "ssp": "50x10x3721, FP64 (the oracle's own precision)",
+                       "sample": "bounded spaxel subset per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -292,26 +340,30 @@ def run_serving(args, dev, ssp):
         res[name] = {"saturated": {"deposits_per_s": float(dep.sum() / mk), "requests_per_s": n_req / mk,
                                    "makespan_s": mk, "deposit_launches": st["deposit_launches"],
                                    "max_batch": st["max_batch"]}}
-    # Poisson arrivals at a fixed rate: args.serve_load x the sequential capacity
-    rate = args.serve_load * res["sequential"]["saturated"]["requests_per_s"]
-    arrivals = unit_arrivals / rate
+    # Poisson arrivals at fixed rates: each load x the sequential capacity
+    loads = [float(x) for x in args.serve_loads.split(",") if x.strip()]
+    cap = res["sequential"]["saturated"]["requests_per_s"]
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    for name, cfg in (("sequential", (1, 1)), ("served", (args.serve_slots, args.serve_batch))):
-        srv = server(*cfg)
-        lat, mk = _drive(torch, srv, dev, reqs, ins, arrivals)
-        st = srv.stats()
-        srv.close()
-        res[name]["poisson"] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                                "mean_ms": 1e3 * float(lat.mean()), "max_ms": 1e3 * float(lat.max()),
-                                "deposits_per_s": float(dep.sum() / mk), "requests_per_s": n_req / mk,
-                                "deposit_launches": st["deposit_launches"], "max_batch": st["max_batch"],
-                                "peak_bytes": st["peak_bytes"]}
+    for rho in loads:
+        arrivals = unit_arrivals / (rho * cap)
+        key = f"poisson_rho{rho:g}"
+        for name, cfg in (("sequential", (1, 1)), ("served", (args.serve_slots, args.serve_batch))):
+            srv = server(*cfg)
+            lat, mk = _drive(torch, srv, dev, reqs, ins, arrivals)
+            st = srv.stats()
+            srv.close()
+            res[name][key] = {"load_vs_sequential_capacity": rho, "arrival_rate_hz": rho * cap,
+                              "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                              "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                              "mean_ms": 1e3 * float(lat.mean()), "max_ms": 1e3 * float(lat.max()),
+                              "deposits_per_s": float(dep.sum() / mk), "requests_per_s": n_req / mk,
+                              "deposit_launches": st["deposit_launches"], "max_batch": st["max_batch"],
+                              "peak_bytes": st["peak_bytes"]}
     clk = clocks.stop()
     del ins, mothers
     res["classes"] = _serve_classes(torch, server, dev, args)
-    return {"requests": n_req, "arrival_rate_hz": rate, "load_vs_sequential_capacity": args.serve_load,
+    return {"requests": n_req, "sequential_capacity_requests_per_s": cap, "loads_vs_sequential_capacity": loads,
             "particles": "log-uniform [1e4, 2e7] (prefixes of 4 device-drawn 3-D disks)",
             "cube_side": "uniform [40, 300] spaxels of 0.2 kpc x 3721 bins",
             "inclination": "uniform [0, 90] deg", "deposits_total": float(dep.sum()),
@@ -374,20 +426,19 @@ def _events_ms(torch, fn, stream, steps, flush):
     return np.array([a.elapsed_time(b) for a, b in ev])
 
 
-def run_extra(args, dev, flush):
+def run_extra(args, dev, flush, peak_tflops):
     import torch
     from paper_2412_08265_gb300 import synth
-    from paper_2412_08265_gb300.model import CubeModel
     stream = torch.cuda.current_stream(dev)
     out = {}
     sel = set(args.extra.split(","))
     wl = synth.mid_galaxy(n=args.particles, seed=1)
+    if "mid_f32" in sel:
+        out["mid_f32"] = _extra_mid_f32(args, dev, flush, stream, peak_tflops)
     if "differentiable" in sel:
         out["differentiable"] = _extra_differentiable(args, dev, flush, wl, stream)
     if "bin_means" in sel:
         out["bin_means"] = _extra_bin_means(args, dev, flush, wl, stream)
-    if "large_bf16" in sel:
-        out["large_bf16"] = _extra_large_bf16(args, dev, flush, stream)
     return out
 
 
@@ -456,30 +507,97 @@ def _extra_bin_means(args, dev, flush, wl, stream):
     return res
 
 
-def _extra_large_bf16(args, dev, flush, stream):
-    """Large galaxy, BF16 templates."""
+def _extra_mid_f32(args, dev, flush, stream, peak_tflops):
+    """Mid-size galaxy, FP32 templates (1e6 particles, 150 x 150 x 3721)."""
     import torch
     from paper_2412_08265_gb300 import synth
     from paper_2412_08265_gb300.model import CubeModel
-    wl = synth.large_galaxy()
-    model = CubeModel(wl.ssp, wl.telescope, "bf16", max_particles=wl.particles.n, device=dev)
+    wl = synth.mid_galaxy(n=args.particles, seed=1)
+    model = CubeModel(wl.ssp, wl.telescope, "f32", max_particles=wl.particles.n, device=dev)
     d = model.device_particles(wl.particles)
     cube = torch.empty(model.cube_shape, dtype=torch.float32, device=dev)
-    for _ in range(2):
+    for _ in range(3):
         model.forward(d, out=cube)
     st = model.stats()
     model.set_profiling(True)
-    t = _events_ms(torch, lambda: model.forward(d, out=cube), stream, 3, flush)
+    t = _events_ms(torch, lambda: model.forward(d, out=cube), stream, max(5, min(args.steps, 20)), flush)
     dep = model.profile_history("deposit")
     psf = model.profile_history("psf_lsf")
     model.set_profiling(False)
+    dep_s = float(np.mean(dep)) / 1e3
+    traffic, tsrc = recorded_traffic(wl.name)
     res = {
         "workload": wl.name, "n_in_fov": st["n_in_fov"], "ms_per_step": float(np.median(t)),
+        "p50_ms": float(np.percentile(t, 50)), "p99_ms": float(np.percentile(t, 99)),
         "deposits_per_s": st["deposits"] / (float(np.median(t)) / 1e3),
-        "deposit_ms": float(np.median(dep)), "psf_lsf_ms": float(np.median(psf)),
+        "deposit_ms": 1e3 * dep_s, "psf_lsf_ms": float(np.median(psf)),
+        "deposit_fp32_tflops": st["deposits"] * FLOPS_PER_DEPOSIT / dep_s / 1e12,
+        "deposit_frac_of_measured_fp32": st["deposits"] * FLOPS_PER_DEPOSIT / dep_s / 1e12 / peak_tflops,
+        "deposit_dram_bytes": traffic, "traffic_source": tsrc,
         "tile_bins": st["tile_w"], "age_bands": st["n_bands"]}
     model.close()
     return res
+
+
+def _e2e(args, dev, wl, dtype, model, stream, deposits):
+    """End to end through the C ABI with host buffers: page-locked particle
+    arrays in, page-locked host cube out, every copy inside the timing. The
+    headline figure is the server (rubix_serve_submit) with a few requests in
+    flight; the synchronous single-handle call is reported beside it."""
+    import torch
+    from paper_2412_08265_gb300 import capi
+    from paper_2412_08265_gb300.serve import Server
+    p = wl.particles
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), dtype=np.float32)).pin_memory()
+            for k in ("x", "y", "v_los", "mass", "age", "Z")}
+    h2d = sum(v.numel() * 4 for v in host.values())
+    cube_bytes = int(np.prod(model.cube_shape)) * 4
+    depth = 3 if cube_bytes < (1 << 30) else 2
+    outs = [torch.empty(model.cube_shape, dtype=torch.float32).pin_memory() for _ in range(depth)]
+    cp = model.c_particles({**{k: v.numpy() for k, v in host.items()}, "preprojected": True,
+                            "inclination": 0.0}, on_device=False)
+    for _ in range(2):
+        capi.rubix_cube_forward(model.handle, cp, 0, 0.0, outs[0].data_ptr(), 0, stream.cuda_stream)
+    k_single = max(3, min(args.steps, 8))
+    t0 = time.perf_counter()
+    for _ in range(k_single):
+        capi.rubix_cube_forward(model.handle, cp, 0, 0.0, outs[0].data_ptr(), 0, stream.cuda_stream)
+    t_single = (time.perf_counter() - t0) / k_single
+    single = {"value": deposits / t_single, "ms_per_step": 1e3 * t_single,
+              "api": "rubix_cube_forward, host buffers, one call at a time (the call returns after the copy)"}
+    budget = max(16 << 30, 3 * depth * model_bytes_estimate(model))
+    srv = Server(wl.ssp, wl.telescope, template_dtype=dtype, hbm_budget_bytes=budget, max_slots=depth, max_batch=1,
+                 device=dev)
+    din = {**host, "preprojected": True, "inclination": 0.0}
+
+    def burst(k):
+        tks = []
+        for i in range(k):
+            if i >= depth and srv.wait(tks[i - depth], 120.0) != 0:
+                raise RuntimeError("served request failed: " + capi.last_error_message())
+            tks.append(srv.submit(wl.telescope, din, outs[i % depth]))
+        for t in tks[max(0, k - depth):]:
+            if srv.wait(t, 120.0) != 0:
+                raise RuntimeError("served request failed: " + capi.last_error_message())
+
+    burst(2 * depth)
+    k_srv = max(3 * depth, min(args.steps, 10) * (2 if depth == 3 else 1))
+    t_bursts = []
+    for _ in range(3):  # three timed bursts; the median is reported
+        t0 = time.perf_counter()
+        burst(k_srv)
+        t_bursts.append((time.perf_counter() - t0) / k_srv)
+    t_srv = float(np.median(t_bursts))
+    srv.close()
+    return {"value": deposits / t_srv, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(cube_bytes), "ms_per_step": 1e3 * t_srv,
+            "api": f"rubix_serve_submit, host buffers (page-locked), {depth} requests in flight, "
+                   f"median of 3 bursts of {k_srv} requests",
+            "burst_ms_per_step": [1e3 * t for t in t_bursts], "single_call": single}
+
+
+def model_bytes_estimate(model) -> int:
+    return int(np.prod(model.cube_shape)) * 4 * 4
 
 
 # ---------------------------------------------------------------------------
@@ -491,7 +609,6 @@ def run_ours(args):
     build()
     from paper_2412_08265_gb300 import synth
     from paper_2412_08265_gb300.model import CubeModel
-    from paper_2412_08265_gb300 import capi
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -501,8 +618,10 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    wl = synth.mid_galaxy(n=args.particles, seed=1 + rank)
-    model = CubeModel(wl.ssp, wl.telescope, "f32", max_particles=wl.particles.n, device=dev)
+    wl = synth.large_galaxy(seed=2 + rank) if args.workload == "large" else synth.mid_galaxy(n=args.particles,
+                                                                                              seed=1 + rank)
+    dtype = wl.template_dtype
+    model = CubeModel(wl.ssp, wl.telescope, dtype, max_particles=wl.particles.n, device=dev)
     d = model.device_particles(wl.particles)
     out = torch.empty(model.cube_shape, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
@@ -513,10 +632,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     st = model.stats()
     n_in, deposits, launches_per_step = st["n_in_fov"], st["deposits"], st["kernel_launches"]
+    # the FP32 roof of the deposit, measured on this device just before the timed steps
+    peak, peak_runs = measured_fp32_peak()
 
     model.set_profiling(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    dep_ms = []
     clocks = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
     if ws > 1:
         torch.distributed.barrier()
@@ -541,60 +661,7 @@ def run_ours(args):
     n_in_all = whole_job(n_in * args.steps, 1.0, device=dev)[1]
     model.set_profiling(False)
 
-    # ---- end to end through the C ABI with host buffers ----
-    e2e = None
-    if rank == 0:
-        p = wl.particles
-        host = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), dtype=np.float32)).pin_memory()
-                for k in ("x", "y", "v_los", "mass", "age", "Z")}
-        cp = model.c_particles({**{k: v.numpy() for k, v in host.items()}, "preprojected": True,
-                                "inclination": 0.0}, on_device=False)
-        hcube = torch.empty(model.cube_shape, dtype=torch.float32).pin_memory()
-        h2d = sum(v.numel() * 4 for v in host.values())
-        d2h = hcube.numel() * 4
-        for _ in range(2):
-            capi.rubix_cube_forward(model.handle, cp, 0, 0.0, hcube.data_ptr(), 0, stream.cuda_stream)
-        k_e2e = max(3, min(args.steps, 10))
-        t0 = time.perf_counter()
-        for _ in range(k_e2e):
-            capi.rubix_cube_forward(model.handle, cp, 0, 0.0, hcube.data_ptr(), 0, stream.cuda_stream)
-        t_e2e = (time.perf_counter() - t0) / k_e2e
-        single = {"value": deposits / t_e2e, "ms_per_step": 1e3 * t_e2e,
-                  "api": "rubix_cube_forward, host buffers, one call at a time (the call returns after the copy)"}
-        # the same galaxy as a stream of requests through the server
-        # (rubix_serve_submit), host inputs and host cubes, a few requests in
-        # flight so that one request's copies overlap another's kernels
-        from paper_2412_08265_gb300.serve import Server
-        depth = 3
-        srv = Server(wl.ssp, wl.telescope, hbm_budget_bytes=16 << 30, max_slots=depth, max_batch=1, device=dev)
-        outs = [torch.empty(model.cube_shape, dtype=torch.float32).pin_memory() for _ in range(depth)]
-        din = {**host, "preprojected": True, "inclination": 0.0}
-
-        def burst(k):
-            tks = []
-            for i in range(k):
-                if i >= depth and srv.wait(tks[i - depth], 60.0) != 0:
-                    raise RuntimeError("served request failed: " + capi.last_error_message())
-                tks.append(srv.submit(wl.telescope, din, outs[i % depth]))
-            for t in tks[max(0, k - depth):]:
-                if srv.wait(t, 60.0) != 0:
-                    raise RuntimeError("served request failed: " + capi.last_error_message())
-
-        burst(2 * depth)
-        k_srv = max(3 * depth, min(args.steps, 10) * 2)
-        t_bursts = []
-        for _ in range(3):  # three timed bursts; the median is reported
-            t0 = time.perf_counter()
-            burst(k_srv)
-            t_bursts.append((time.perf_counter() - t0) / k_srv)
-        t_srv = float(np.median(t_bursts))
-        srv.close()
-        e2e = {"value": deposits / t_srv, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_srv,
-               "api": f"rubix_serve_submit, host buffers (page-locked), {depth} requests in flight, "
-                      f"median of 3 bursts of {k_srv} requests",
-               "burst_ms_per_step": [1e3 * t for t in t_bursts],
-               "single_call": single}
+    e2e = _e2e(args, dev, wl, dtype, model, stream, deposits) if rank == 0 else None
 
     if rank != 0:
         if ws > 1:
@@ -602,17 +669,16 @@ def run_ours(args):
         return 0
 
     # ---- roofline of the dominant kernel (deposit) ----
-    peaks = measured_peaks()
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
-    peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
     dep_avg_s = float(np.mean(dep_ms)) / 1e3
     achieved = deposits * FLOPS_PER_DEPOSIT / dep_avg_s / 1e12
-    traffic = DEPOSIT_TRAFFIC_BYTES if args.particles == 1_000_000 else None
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": traffic,
+    traffic, traffic_src = recorded_traffic(wl.name)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
+            "frac": achieved / peak["tflops"], "traffic": traffic,
             "kernel": "k_deposit", "kernel_ms": 1e3 * dep_avg_s,
-            "peak_basis": f"FP32 FMA pipe: {n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+            "peak_basis": (f"measured on this GPU before the timed steps: {peak['kind']} dependent-chain benchmark "
+                           f"(rubix_measure_fp32_peak), {peak['fma_per_clk_per_sm']:.1f} FMA/clk/SM at "
+                           f"{peak['sm_mhz']:.0f} MHz"),
+            "peak_runs": peak_runs, "traffic_source": traffic_src,
             "deposits_per_launch": deposits, "flops_per_deposit": FLOPS_PER_DEPOSIT}
 
     # ---- CPU baseline: the oracle on a bounded sample, and the sampled rel err ----
@@ -630,25 +696,30 @@ def run_ours(args):
         got = got.cpu().numpy().astype(np.float64)
         rel = float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
 
+    tel = wl.telescope
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "n_particles": wl.particles.n, "n_in_fov": n_in,
-                       "spaxels": "150x150", "spaxel_kpc": 0.2, "n_lambda": 3721, "ssp": "50x10x3721 f32",
-                       "psf_fwhm_spaxels": 1.5, "lsf_sigma_A": 1.2, "l2": "flushed between timed steps",
-                       "parallelism": f"replicas x{ws}"},
+                       "spaxels": f"{tel.nx}x{tel.ny}", "spaxel_kpc": tel.spaxel_size, "n_lambda": tel.n_lambda,
+                       "ssp": f"50x10x3721 stored {dtype}, FP32 arithmetic",
+                       "psf_fwhm_spaxels": tel.psf_fwhm, "lsf_sigma_A": tel.lsf_sigma,
+                       "l2": "flushed between timed steps", "parallelism": f"replicas x{ws}"},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-            "rel_err_bound": REL_ERR_BOUND, "rel_err_sampled": rel,
+            "rel_err_bound": REL_ERR_BOUND[dtype], "rel_err_sampled": rel,
             "particles_per_s": n_in_all / total_s,
             "clocks": clk, "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "stage_ms_median": stage_med}
-    if not args.no_extra:
-        line["workloads"] = run_extra(args, dev, flush)
-    if args.serve_requests > 0:
-        line["serving"] = run_serving(args, dev, wl.ssp)
-    print(json.dumps(line), flush=True)
+            "stage_ms_median": stage_med,
+            "deposit_geometry": {"tile_bins": st["tile_w"], "slab_nodes": st["slab_w"], "age_bands": st["n_bands"]}}
     model.close()
+    del d, out
+    torch.cuda.empty_cache()
+    if not args.no_extra:
+        line["workloads"] = run_extra(args, dev, flush, peak["tflops"])
+    if args.serve_requests > 0:
+        line["serving"] = run_serving(args, dev, synth.mid_galaxy(n=1000, seed=1).ssp)
+    print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -666,14 +737,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--particles", type=int, default=1_000_000,
                     help="particles of the mid-size galaxy (smaller only for profiler captures)")
-    ap.add_argument("--extra", default="differentiable,bin_means,large_bf16",
+    ap.add_argument("--workload", default="large", choices=["large", "mid"],
+                    help="workload of the timed steps (large: the largest single-GPU configuration)")
+    ap.add_argument("--extra", default="mid_f32,differentiable,bin_means",
                     help="comma-separated extra workloads reported under 'workloads'")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the differentiable-step and large-galaxy measurements")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests in the serving stream (0 = no serving run)")
-    ap.add_argument("--serve-load", type=float, default=0.9,
-                    help="Poisson arrival rate as a fraction of the sequential path's capacity")
+    ap.add_argument("--serve-loads", default="0.5,0.9",
+                    help="Poisson arrival rates, as fractions of the sequential path's capacity")
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-batch", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)

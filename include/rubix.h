@@ -107,6 +107,14 @@ typedef struct rubix_telescope {
                                      * interpolation between template nodes);
                                      * 1 = its mean over each bin [lambda_j - dlambda/2,
                                      * lambda_j + dlambda/2] (flux-conserving rebinning). */
+    int32_t row_lo, row_hi;         /* row window: only spaxel rows [row_lo, row_hi) of the
+                                     * ny-row field are modelled (0, 0 = all rows). Spaxel keys
+                                     * are computed on the whole field, so a row-sharded galaxy
+                                     * (each shard its own rows) gets bitwise the unsharded
+                                     * assignment; particles of other rows are dropped. The
+                                     * cube then has row_hi - row_lo rows, PSF and LSF see zero
+                                     * padding at its edges, noise is keyed by the window's own
+                                     * voxel index. */
 } rubix_telescope;
 
 /* Star particles (Sec. 3: input handler fields), float32 structure of arrays.
@@ -183,7 +191,9 @@ rubix_status rubix_cube_backward(rubix_cube_t *h, uint64_t forward_tag, const fl
 rubix_status rubix_cube_destroy(rubix_cube_t *h);
 
 /* Spaxel assignment only (orientation + key, bit-exact definition above):
- * keys_out (device int32 [n]) gets iy*nx + ix, or nx*ny for particles outside. */
+ * keys_out (device int32 [n]) gets iy*nx + ix, or nx*ny for particles outside
+ * (with a row window: (iy - row_lo)*nx + ix, or nx*(row_hi - row_lo) for
+ * particles outside the window). */
 rubix_status rubix_cube_spaxel_keys(rubix_cube_t *h, const rubix_particles *p, int32_t *keys_out,
                                     void *stream);
 
@@ -224,20 +234,48 @@ rubix_status rubix_cube_stats(rubix_cube_t *h, int64_t *stats, int32_t *n_inout)
  * allocator (a framework's caching allocator, a pool sized at start-up) owns
  * the device's memory budget, or when the call runs in a latency-critical
  * loop where cudaMalloc/cudaFree would synchronise the device.
- * Same result as rubix_cube_forward's sort (rubix_cube_sorted): perm_out
- * (device int32 [n]) lists particle indices by spaxel key, ties by index;
- * seg_off_out (device int32 [nx*ny + 2]) gives the first sorted position of
- * each key, then n. Particles must be device pointers (on_device = 1); only
- * x, y (and z when preprojected = 0) are read. Scratch lives in one fixed
+ * The stable sort of the particles by spaxel key (the key of
+ * rubix_cube_spaxel_keys): perm_out (device int32 [n]) lists particle indices
+ * by key, ties by index; seg_off_out (device int32 [nx*ny + 2]) gives the
+ * first sorted position of each key, then n (entry nx*ny = particles in the
+ * field). (rubix_cube_sorted orders each spaxel's particles by SSP age band
+ * first; its segment offsets are the same.) Particles must be device pointers (on_device = 1); only
+ * x, y (and z when preprojected = 0) are read; the telescope's row window is
+ * not applied (the whole field is sorted). Scratch lives in one fixed
  * device array inside the library (about 4.3 MB, held on every device that
  * loads the library until exit). Limits: n <= 262144 and nx*ny <= 262143;
- * larger problems return RUBIX_ERR_INVALID_ARG with a message. The first call
+ * larger problems return RUBIX_ERR_INVALID_ARG with a message (and
+ * RUBIX_ERR_UNSUPPORTED if the sort's scratch ever outgrew the array). The first call
  * on a device looks up the array's device address (once per device, with that
  * device current); make that first call before any stream capture. All calls
  * share the array: calls whose work overlaps on the GPU (other streams or
  * threads without ordering) race and give wrong results. */
 rubix_status rubix_spaxel_sort_noalloc(const rubix_particles *p, const rubix_telescope *tel,
                                        int32_t *perm_out, int32_t *seg_off_out, void *stream);
+
+/* PSF then LSF of a telescope (Sec. 4: Gaussian responses; the readings above)
+ * applied to a device cube: cube_in and cube_out are float32
+ * [n_rows][nx][n_lambda] (dense, distinct buffers), zero padded at the cube's
+ * borders, no noise; the telescope's row window is not used (n_rows gives the
+ * cube's rows). This is the convolution rubix_cube_forward applies after the
+ * deposit, bit for bit, so a row-sharded galaxy can convolve each shard's rows
+ * together with r_psf halo rows taken from its neighbours (Sec. 4's
+ * multi-device runs). May allocate scratch on `stream` for radii without a
+ * fused kernel. Errors: INVALID_ARG, CUDA, OOM. */
+rubix_status rubix_convolve(const rubix_telescope *tel, const float *cube_in, float *cube_out, int32_t n_rows,
+                            void *stream);
+
+/* Measured FP32 FMA throughput of the current device (no counterpart in the
+ * paper: the denominator of the deposit kernel's FP32 roofline, measured on
+ * the machine and at the clocks the deposit runs at). Runs eight independent
+ * chains of FFMA (packed = 0) or packed FFMA2 (packed = 1) in every thread of
+ * four 512-thread blocks per SM for about a millisecond, on the legacy
+ * default stream, and synchronises. Outputs (host pointers, the last two
+ * nullable): flops_per_s (2 per FMA); FMAs per clock per SM; the SM clock in
+ * MHz during the run (clock64 against the global timer).
+ * Errors: INVALID_ARG, CUDA. */
+rubix_status rubix_measure_fp32_peak(int32_t packed, double *flops_per_s, double *fma_per_clk_per_sm,
+                                     double *sm_mhz);
 
 /* ---------------------------------------------------------------------------
  * Serving: many galaxies through one resident SSP grid.

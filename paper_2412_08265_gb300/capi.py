@@ -45,7 +45,7 @@ class rubix_telescope(C.Structure):
                 ("n_lambda", C.c_int32), ("lambda0", C.c_double), ("dlambda", C.c_double),
                 ("psf_fwhm", C.c_double), ("lsf_sigma", C.c_double), ("psf_radius", C.c_int32),
                 ("lsf_radius", C.c_int32), ("z_cosmo", C.c_double), ("flux_scale", C.c_double),
-                ("resample", C.c_int32)]
+                ("resample", C.c_int32), ("row_lo", C.c_int32), ("row_hi", C.c_int32)]
 
 
 class rubix_particles(C.Structure):
@@ -95,6 +95,8 @@ _SIGS = {
     "rubix_serve_stats": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "rubix_serve_destroy": (C.c_int32, [C.c_void_p]),
     "rubix_selftest_bounded_wait": (C.c_int32, [C.c_double, C.POINTER(C.c_int32)]),
+    "rubix_measure_fp32_peak": (C.c_int32, [C.c_int32, _dp, _dp, _dp]),
+    "rubix_convolve": (C.c_int32, [C.POINTER(rubix_telescope), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "rubix_last_error_message": (C.c_char_p, []),
     "rubix_version": (C.c_char_p, []),
 }
@@ -264,6 +266,19 @@ def rubix_selftest_bounded_wait(limit_s: float) -> bool:
     t = C.c_int32(0)
     _call("rubix_selftest_bounded_wait", C.c_double(limit_s), C.byref(t))
     return bool(t.value)
+
+
+def rubix_convolve(tel: rubix_telescope, cube_in: int, cube_out: int, n_rows: int, stream: int) -> None:
+    _call("rubix_convolve", C.byref(tel), C.c_void_p(cube_in), C.c_void_p(cube_out), C.c_int32(n_rows),
+          C.c_void_p(stream))
+
+
+def rubix_measure_fp32_peak(packed: bool) -> tuple[float, float, float]:
+    """(FLOP/s, FMAs per clock per SM, SM MHz) of an FFMA (packed=False) or
+    FFMA2 (packed=True) chain benchmark on the current device."""
+    f, r, m = C.c_double(), C.c_double(), C.c_double()
+    _call("rubix_measure_fp32_peak", C.c_int32(1 if packed else 0), C.byref(f), C.byref(r), C.byref(m))
+    return float(f.value), float(r.value), float(m.value)
 
 
 def rubix_last_error_message() -> str:

@@ -471,7 +471,6 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
                         else
                             S = adj_particle<R>(P.wu[q], rec4[2 * q + 1], C, slab, P.quad, lane, lanef, G, grow,
                                                 P.ls0_over);
-#if RUBIX_ADJ_XRED
                         // the four sums over the warp with 6 shuffles: halves of the
                         // warp trade pairs, quarters trade singles, then a butterfly
                         // over 8 lanes; lane 8 v ends with sum v (v = sm, sa, sz, sv)
@@ -483,16 +482,6 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
 #pragma unroll
                         for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
                         if ((lane & 7) == 0) reinterpret_cast<float*>(part + q)[lane >> 3] = c;
-#else
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            S.sm += __shfl_xor_sync(0xffffffffu, S.sm, o);
-                            S.sa += __shfl_xor_sync(0xffffffffu, S.sa, o);
-                            S.sz += __shfl_xor_sync(0xffffffffu, S.sz, o);
-                            S.sv += __shfl_xor_sync(0xffffffffu, S.sv, o);
-                        }
-                        if (lane == 0) part[q] = make_float4(S.sm, S.sa, S.sz, S.sv);
-#endif
                     }
                 }
             }

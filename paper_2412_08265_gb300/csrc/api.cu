@@ -243,6 +243,45 @@ extern "C" rubix_status rubix_cube_stats(rubix_cube_t* h, int64_t* stats, int32_
 }
 
 // ----------------------------------------------------------------------------
+// PSF + LSF of a given device cube
+// ----------------------------------------------------------------------------
+extern "C" rubix_status rubix_convolve(const rubix_telescope* tel, const float* cube_in, float* cube_out,
+                                       int32_t n_rows, void* stream) {
+    if (!tel || !cube_in || !cube_out) return fail(RUBIX_ERR_INVALID_ARG, "NULL argument");
+    if (cube_in == cube_out) return fail(RUBIX_ERR_INVALID_ARG, "cube_in and cube_out must be distinct");
+    if (n_rows < 1 || tel->nx < 1 || (long long)tel->nx * n_rows >= (1ll << 24) || tel->n_lambda < 1 ||
+        tel->n_lambda > 8192 || !(tel->dlambda > 0.0) || !(tel->psf_fwhm >= 0.0) || !(tel->lsf_sigma >= 0.0))
+        return fail(RUBIX_ERR_INVALID_ARG, "cube or telescope sizes out of range");
+    ConvParams C{};
+    const bool conv = conv_params(tel, n_rows, &C);
+    if (C.rp > kMaxRadius || C.rl > kMaxRadius) return fail(RUBIX_ERR_INVALID_ARG, "PSF/LSF radius > 64");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)n_rows * tel->nx * tel->n_lambda * sizeof(float);
+    if (!conv) {
+        CK(cudaMemcpyAsync(cube_out, cube_in, bytes, cudaMemcpyDeviceToDevice, st));
+        return RUBIX_OK;
+    }
+    unsigned* d_err = nullptr;
+    float* tmp = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&d_err), 16, st));
+    CK(cudaMemsetAsync(d_err, 0, 16, st));
+    C.err = d_err;
+    if (psf_lsf_needs_tmp(C.rp, C.rl)) {
+        const cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), bytes, st);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(d_err, st);
+            return fail(RUBIX_ERR_OOM, "rubix_convolve scratch: %s", cudaGetErrorString(e));
+        }
+    }
+    const int l = launch_psf_lsf(C, cube_in, tel->n_lambda, nullptr, tmp, cube_out, st);
+    if (tmp) cudaFreeAsync(tmp, st);
+    cudaFreeAsync(d_err, st);
+    if (l < 0) return fail(RUBIX_ERR_CUDA, "PSF/LSF launch failed");
+    CK(cudaGetLastError());
+    return RUBIX_OK;
+}
+
+// ----------------------------------------------------------------------------
 // backward
 // ----------------------------------------------------------------------------
 extern "C" rubix_status rubix_cube_forward_tag(rubix_cube_t* h, uint64_t* tag) {

@@ -101,7 +101,7 @@ __global__ void k_setup(SetupParams P) {
 int launch_setup(const SetupParams& P, long long n_total, cudaStream_t st) {
     if (n_total <= 0) return 0;
     long long nb = (n_total + 255) / 256;
-    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb > 16ll * sm_count()) nb = 16ll * sm_count();
     k_setup<<<(int)nb, 256, 0, st>>>(P);
     return 1;
 }
@@ -203,7 +203,6 @@ __device__ __forceinline__ void fast_rounds(const float4 w4, const float4* __res
     const int s31 = 31 * ncb, s30 = 30 * ncb;
     const float nld = -lanef * delta;
     const float d31 = 31.f * delta;
-#if RUBIX_DEP_PAIR2
     // rounds two at a time: the per-bin arithmetic in packed FP32x2
 #pragma unroll
     for (int r = 0; r + 1 < R; r += 2) {
@@ -238,20 +237,6 @@ __device__ __forceinline__ void fast_rounds(const float4 w4, const float4* __res
         const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
         acc[R - 1] += fmaf(fabsf(g), X - M, M);
     }
-#else
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const float M = quad_dot(w4, *q);
-        const float g = f + nld;
-        const float X = __shfl_sync(0xffffffffu, M, g < 0.f ? lane - 1 : lane + 1);
-        acc[r] += fmaf(fabsf(g), X - M, M);
-        // the next round starts 31 dt/dj = 31 - 31 delta nodes further on
-        f -= d31;
-        const bool carry = f < 0.f;
-        f = carry ? f + 1.f : f;
-        q += carry ? s30 : s31;
-    }
-#endif
 }
 
 // General path (out of line; rare on the workloads here): each bin's node
@@ -333,7 +318,6 @@ __device__ __forceinline__ void mean_rounds(const float4 w4, const float4* __res
     const float d30 = 30.f * delta;
     const float iA = 1.f / (1.f - delta);
     const int lp = lane + 1, lm = lane - 1;
-#if RUBIX_DEP_PAIR2
     // rounds two at a time: the per-bin arithmetic in packed FP32x2
 #pragma unroll
     for (int r = 0; r + 1 <= R; r += 2) {
@@ -380,28 +364,6 @@ __device__ __forceinline__ void mean_rounds(const float4 w4, const float4* __res
         const float ai = fmaf(-g, iA, up ? iA : 0.f);
         acc[R] += fmaf(ai, L - Ln, (up ? X : M) + Ln);
     }
-#else
-#pragma unroll
-    for (int r = 0; r <= R; ++r) {
-        float4 Q = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < R || lane <= R + 1) Q = *q;
-        const float M = quad_dot(wh, Q);
-        const float g = f + nld;
-        const bool up = g >= 0.f;
-        const float X = __shfl_sync(0xffffffffu, M, up ? lp : lm);
-        const float L = fmaf(fabsf(g), X - M, M);
-        const float Ln = __shfl_down_sync(0xffffffffu, L, 1);
-        const float ai = fmaf(-g, iA, up ? iA : 0.f);  // a / A
-        acc[r] += fmaf(ai, L - Ln, (up ? X : M) + Ln);
-        if (r < R) {
-            // the next round starts at edge 30, 30 - 30 delta nodes further on
-            f -= d30;
-            const bool carry = f < 0.f;
-            f = carry ? f + 1.f : f;
-            q += carry ? s29 : s30;
-        }
-    }
-#endif
 }
 
 // General path of the bin means: bin j (owned = a bin of this tile held by
@@ -491,11 +453,6 @@ __global__ void k_job_cost(const DepositParams P, long long* job_cost) {
 }
 
 constexpr int kJobChunk = 32;  // jobs per shared-memory work table
-// Particle records: 1 = the next one loaded into registers ahead, 2 = the next
-// one prefetched into L1.
-#ifndef RUBIX_DEP_RECPF
-#define RUBIX_DEP_RECPF 2
-#endif
 
 // One work item's particles [q0, q1) of the current band, accumulated in
 // registers in sorted order, then stored (band 0) or added (later bands) to
@@ -509,12 +466,6 @@ __device__ __forceinline__ void deposit_item(const DepositParams& P, const TileC
     float acc[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = 0.f;
-#if !RUBIX_DEP_BANDADD
-    // later bands add to the row: start moving it into L2 now
-    if (band > 0 && lane < R && C.j0 + 31 * lane < P.n_lambda)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(dst + C.j0 + 31 * lane));
-#endif
-#if RUBIX_DEP_RECPF == 2
     // the next particle's record is pulled into L1 while the current one is
     // deposited (no registers held across the particle)
     if (q0 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * q0));
@@ -526,25 +477,6 @@ __device__ __forceinline__ void deposit_item(const DepositParams& P, const TileC
         else
             deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
     }
-#else
-    // the next particle's record is in flight while the current one is deposited
-    float4 wn, gn;
-    if (q0 < q1) {
-        wn = rec4[2 * q0];
-        gn = rec4[2 * q0 + 1];
-    }
-    for (int q = q0; q < q1; ++q) {
-        const float4 w4 = wn, g4 = gn;
-        if (q + 1 < q1) {
-            wn = rec4[2 * (q + 1)];
-            gn = rec4[2 * (q + 1) + 1];
-        }
-        if constexpr (MEAN)
-            mean_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
-        else
-            deposit_particle<R>(w4, g4, C, slab, P.quad, lane, lanef, acc, P.slow_count);
-    }
-#endif
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int j = MEAN ? C.j0 + 30 * r + lane : C.j0 + 31 * r + lane;
@@ -553,13 +485,9 @@ __device__ __forceinline__ void deposit_item(const DepositParams& P, const TileC
             if (band == 0) {
                 dst[j] = acc[r];
             } else {
-#if RUBIX_DEP_BANDADD
                 // one reduction per address and band, bands ordered by the
                 // CTA barrier: the sum order is fixed
                 atomicAdd(dst + j, acc[r]);
-#else
-                dst[j] += acc[r];
-#endif
             }
         }
     }
@@ -766,7 +694,8 @@ __global__ void k_combine(const int* __restrict__ part_off, int n_s, int n_lambd
 
 int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube, int pitch,
                    cudaStream_t st) {
-    int nb = n_s < 152 * 8 ? n_s : 152 * 8;
+    const int cap = 8 * sm_count();
+    int nb = n_s < cap ? n_s : cap;
     if (nb < 1) return 0;
     k_combine<<<nb, 256, 0, st>>>(part_off, n_s, n_lambda, partials, cube, pitch);
     return 1;

@@ -145,6 +145,8 @@ rubix_status validate_telescope(const rubix_telescope* tel, double ssp_dlambda) 
     if (!(tel->psf_fwhm >= 0.0) || !(tel->lsf_sigma >= 0.0)) return fail(RUBIX_ERR_INVALID_ARG, "negative PSF/LSF width");
     if (!(tel->z_cosmo > -1.0)) return fail(RUBIX_ERR_INVALID_ARG, "z_cosmo must be > -1");
     if (tel->resample != 0 && tel->resample != 1) return fail(RUBIX_ERR_INVALID_ARG, "resample must be 0 or 1");
+    if (!(tel->row_lo == 0 && tel->row_hi == 0) && !(tel->row_lo >= 0 && tel->row_lo < tel->row_hi && tel->row_hi <= tel->ny))
+        return fail(RUBIX_ERR_INVALID_ARG, "row window must satisfy 0 <= row_lo < row_hi <= ny (or 0, 0 for all rows)");
     if (tel->dlambda / ((1.0 + tel->z_cosmo) * ssp_dlambda) > 3.0)
         return fail(RUBIX_ERR_INVALID_ARG, "instrument bins wider than 3 SSP steps are not supported");
     const double sp = tel->psf_fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
@@ -190,6 +192,8 @@ void orientation_matrix(double inclination, double azimuth, double position_angl
     Da[0] = si * ca;
     Da[1] = -(si * sa);
 }
+
+int window_rows(const rubix_telescope* tel) { return (tel->row_hi > 0) ? tel->row_hi - tel->row_lo : tel->ny; }
 
 bool same_wavelength_grid(const SspState& S, const rubix_telescope* tel) {
     return tel->n_lambda == S.n_lambda && tel->lambda0 == S.lambda0 && tel->dlambda == S.dlambda &&
@@ -469,13 +473,27 @@ int conv_radius_lsf(const rubix_telescope* tel) {
 
 }  // namespace
 
+bool conv_params(const rubix_telescope* tel, int rows, ConvParams* C) {
+    C->nx = tel->nx;
+    C->ny = rows;
+    C->n_lambda = tel->n_lambda;
+    const double sp = tel->psf_fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    const double sl = tel->lsf_sigma / tel->dlambda;
+    C->rp = conv_radius_psf(tel);
+    C->rl = conv_radius_lsf(tel);
+    if (sp > 0.0) gauss_kernel(sp, C->rp, C->gp); else C->gp[0] = 1.f;
+    if (sl > 0.0) gauss_kernel(sl, C->rl, C->gl); else C->gl[0] = 1.f;
+    C->noise_inv_s2n = 0.f;
+    return (sp > 0.0) || (sl > 0.0);
+}
+
 size_t plan_bytes(const SspState& S, const rubix_telescope* tel, long long n, bool with_out, bool with_grad,
                   bool staging) {
     Plan tmp;
     const int rp = conv_radius_psf(tel), rl = conv_radius_lsf(tel);
     const bool need_tmp = psf_lsf_needs_tmp(rp, rl);
     size_t total = 0;
-    for (const Buf& b : plan_buffers(&tmp, S, tel->nx * tel->ny, tel->n_lambda, n, with_out, with_grad, need_tmp,
+    for (const Buf& b : plan_buffers(&tmp, S, tel->nx * window_rows(tel), tel->n_lambda, n, with_out, with_grad, need_tmp,
                                      staging, cube0_pitch(rp, rl, tel->n_lambda)))
         total += round256(b.bytes);
     return total;
@@ -514,21 +532,14 @@ rubix_status plan_init(Plan* P, const SspState* S, const rubix_telescope* tel, l
     P->alloc = a;
     P->tel = *tel;
     if (P->tel.flux_scale == 0.0) P->tel.flux_scale = 1.0;
-    P->n_s = tel->nx * tel->ny;
+    P->rows = window_rows(tel);
+    P->row_lo = (tel->row_hi > 0) ? tel->row_lo : 0;
+    P->n_s = tel->nx * P->rows;
     P->x_lo = (-0.5 * (double)tel->nx) * tel->spaxel_size;
     P->y_lo = (-0.5 * (double)tel->ny) * tel->spaxel_size;
     P->inv_size = 1.0 / tel->spaxel_size;
     ConvParams& C = P->conv;
-    C.nx = tel->nx;
-    C.ny = tel->ny;
-    C.n_lambda = tel->n_lambda;
-    const double sp = tel->psf_fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
-    const double sl = tel->lsf_sigma / tel->dlambda;
-    C.rp = conv_radius_psf(tel);
-    C.rl = conv_radius_lsf(tel);
-    if (sp > 0.0) gauss_kernel(sp, C.rp, C.gp); else C.gp[0] = 1.f;
-    if (sl > 0.0) gauss_kernel(sl, C.rl, C.gl); else C.gl[0] = 1.f;
-    P->need_conv = (sp > 0.0) || (sl > 0.0);
+    P->need_conv = conv_params(tel, P->rows, &C);
     C.err = S->d_err;
     P->pitch0 = cube0_pitch(C.rp, C.rl, tel->n_lambda);
     P->has_conv_map = false;
@@ -563,7 +574,7 @@ rubix_status plan_init(Plan* P, const SspState* S, const rubix_telescope* tel, l
             plan_release(P);
             return fail(RUBIX_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
         }
-        cuuint64_t gdim[3] = {(cuuint64_t)tel->n_lambda, (cuuint64_t)tel->nx, (cuuint64_t)tel->ny};
+        cuuint64_t gdim[3] = {(cuuint64_t)tel->n_lambda, (cuuint64_t)tel->nx, (cuuint64_t)P->rows};
         cuuint64_t gstr[2] = {(cuuint64_t)P->pitch0 * 4, (cuuint64_t)P->pitch0 * 4 * (cuuint64_t)tel->nx};
         cuuint32_t bx[3] = {box[0], box[1], 1};
         cuuint32_t es[3] = {1, 1, 1};
@@ -634,6 +645,8 @@ AssignParams assign_params(const Plan& P, const rubix_particles* p, const float*
     A.inv_size = P.inv_size;
     A.nx = P.tel.nx;
     A.ny = P.tel.ny;
+    A.row_lo = P.row_lo;
+    A.rows = P.rows;
     A.n_bands = 1;
     return A;
 }

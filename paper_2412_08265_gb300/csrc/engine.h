@@ -50,6 +50,12 @@ rubix_status validate_telescope(const rubix_telescope* tel, double ssp_dlambda);
 rubix_status ssp_state_create(const rubix_ssp_grid* ssp, const rubix_telescope* wavelength_grid, SspState** out);
 void ssp_state_destroy(SspState* S);
 bool same_wavelength_grid(const SspState& S, const rubix_telescope* tel);
+// Spaxel rows the telescope's row window models (ny without a window).
+int window_rows(const rubix_telescope* tel);
+// PSF/LSF parameters of a telescope for a cube of `rows` spaxel rows (kernel
+// radii and normalised Gaussian weights, no noise); false if the telescope
+// has neither a PSF nor an LSF.
+bool conv_params(const rubix_telescope* tel, int rows, ConvParams* C);
 // Particle descriptor checks shared by every entry point (arrays present, n in range).
 rubix_status check_particles(const rubix_particles* p);
 // Orientation R = Rz(position_angle) Rx(inclination) Rz(azimuth), row-major,
@@ -74,7 +80,8 @@ struct Alloc {
 struct Plan {
     const SspState* S = nullptr;
     rubix_telescope tel{};
-    int n_s = 0;
+    int n_s = 0;                            // spaxels of the modelled rows: nx * rows
+    int rows = 0, row_lo = 0;               // the telescope's row window (all ny rows: 0, ny)
     double x_lo = 0, y_lo = 0, inv_size = 0;
     ConvParams conv{};
     bool need_conv = false;

@@ -43,15 +43,6 @@ int sm_count();
 #ifndef RUBIX_DEP_BANDS
 #define RUBIX_DEP_BANDS 0
 #endif
-// 1: the fast path's rounds two at a time in packed FP32x2 arithmetic.
-#ifndef RUBIX_DEP_PAIR2
-#define RUBIX_DEP_PAIR2 1
-#endif
-// 1: the adjoint's four per-particle sums reduced over the warp with 6
-// shuffles (pairs, then singles, then a butterfly); 0: 20 (one butterfly each).
-#ifndef RUBIX_ADJ_XRED
-#define RUBIX_ADJ_XRED 1
-#endif
 // Cost of a work item in particle units, for the static split of the
 // (tile, item) cost space over CTAs.
 #ifndef RUBIX_DEP_COSTC0
@@ -60,12 +51,6 @@ int sm_count();
 // Work items a warp claims at once (its first lanes look them up together).
 #ifndef RUBIX_DEP_GRAB
 #define RUBIX_DEP_GRAB 4
-#endif
-// How later age bands add to a row the first band wrote: 0 = load, add,
-// store (the row prefetched to L2 when the item starts); 1 = in-order
-// reductions at L2.
-#ifndef RUBIX_DEP_BANDADD
-#define RUBIX_DEP_BANDADD 1
 #endif
 
 // K1 parameters. The sort key is spaxel * n_bands + age band (n_bands <= 1:
@@ -80,6 +65,7 @@ struct AssignParams {
     float2* dv_dang;  // [n] original order (nullable): (dv_los/d inclination, dv_los/d azimuth)
     double x_lo, y_lo, inv_size;
     int nx, ny;
+    int row_lo, rows; // row window: spaxel rows [row_lo, row_lo + rows) are kept (rows <= 0: all ny)
     int* key;         // [n]
     double* v_out;    // [n] line-of-sight velocity (nullable)
     // age bands (optional)

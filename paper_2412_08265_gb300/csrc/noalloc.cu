@@ -54,6 +54,8 @@ namespace rubix {
 void set_last_error(const char* msg);  // the thread-local message behind rubix_last_error_message()
 }
 
+static long long n_or_1(long long n) { return n > 0 ? n : 1; }
+
 // The host-side name `g_noalloc_scratch` is only a stand-in for the device
 // array: its device address is fetched once per device (with that device
 // current) and handed to the kernels.
@@ -91,6 +93,13 @@ extern "C" rubix_status rubix_spaxel_sort_noalloc(const rubix_particles* p, cons
     if (p->n > 0 && (!p->x || !p->y)) return bad("x, y required");
     if (p->n > 0 && !p->preprojected && !p->z) return bad("z required when not preprojected");
 
+    // the sort's scratch layout (tiles, digit buckets, scan tiles) must fit
+    // the fixed array; a change of those constants shows up here, not as an
+    // overrun
+    if ((long long)sort_scratch_ints(n_or_1(p->n)) > kNoallocSortInts) {
+        set_last_error("internal: the sort needs more scratch than the no-allocation array holds");
+        return RUBIX_ERR_UNSUPPORTED;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         set_last_error("no CUDA device");

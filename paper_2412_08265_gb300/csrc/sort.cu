@@ -15,7 +15,8 @@ namespace rubix {
 // x_lo = (-0.5 nx) size; u = (x' - x_lo) * (1/size); every FP64 op rounded
 // once (explicit _rn intrinsics), so the integer key is bit-identical to a
 // host evaluation of the same expression. Pre-projected input takes (x', y',
-// v_los) as given.
+// v_los) as given. With a row window the key counts rows from its first row and
+// particles of other rows are dropped like those outside the field.
 // With age bands the sort key appends the particle's band (an internal
 // partition of the SSP grid used by the deposit) below the spaxel index.
 // ----------------------------------------------------------------------------
@@ -47,9 +48,12 @@ __global__ void k_assign(AssignParams P) {
         double u = __dmul_rn(__dsub_rn(xp, P.x_lo), P.inv_size);
         double w = __dmul_rn(__dsub_rn(yp, P.y_lo), P.inv_size);
         const int nb = P.n_bands > 1 ? P.n_bands : 1;
+        const int rows = P.rows > 0 ? P.rows : P.ny;
         int key;
-        if (u >= 0.0 && u < (double)P.nx && w >= 0.0 && w < (double)P.ny) {
-            key = ((int)w * P.nx + (int)u) * nb;
+        // the spaxel row on the whole field, then the row window
+        const int iy = (w >= 0.0 && w < (double)P.ny) ? (int)w - P.row_lo : -1;
+        if (u >= 0.0 && u < (double)P.nx && iy >= 0 && iy < rows) {
+            key = (iy * P.nx + (int)u) * nb;
             if (nb > 1) {
                 int ia;
                 float ta, dta;
@@ -57,7 +61,7 @@ __global__ void k_assign(AssignParams P) {
                 key += age_band(ia, P.apb, nb);
             }
         } else {
-            key = P.nx * P.ny * nb;
+            key = P.nx * rows * nb;
         }
         P.key[p] = key;
         if (P.v_out) P.v_out[p] = v;

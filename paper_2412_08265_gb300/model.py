@@ -52,11 +52,18 @@ class CubeModel:
                                     float(tel.lambda0), float(tel.dlambda), float(tel.psf_fwhm),
                                     float(tel.lsf_sigma), int(tel.psf_radius), int(tel.lsf_radius),
                                     float(tel.z_cosmo), float(tel.flux_scale),
-                                    int(getattr(tel, "resample", 0)))
+                                    int(getattr(tel, "resample", 0)), int(getattr(tel, "row_lo", 0)),
+                                    int(getattr(tel, "row_hi", 0)))
+
+    @staticmethod
+    def rows(tel) -> int:
+        """Spaxel rows of the cube: the row window's, else all ny."""
+        hi = int(getattr(tel, "row_hi", 0))
+        return hi - int(getattr(tel, "row_lo", 0)) if hi > 0 else tel.ny
 
     @property
     def cube_shape(self):
-        return (self.tel.ny, self.tel.nx, self.tel.n_lambda)
+        return (self.rows(self.tel), self.tel.nx, self.tel.n_lambda)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -139,7 +146,7 @@ class CubeModel:
     def sorted(self, stream=None):
         n = int(self._last["mass"].shape[0])
         perm = torch.empty(n, dtype=torch.int32, device=self.device)
-        seg = torch.empty(self.tel.nx * self.tel.ny + 2, dtype=torch.int32, device=self.device)
+        seg = torch.empty(self.tel.nx * self.rows(self.tel) + 2, dtype=torch.int32, device=self.device)
         st = stream or torch.cuda.current_stream(self.device)
         capi.rubix_cube_sorted(self.handle, perm.data_ptr(), seg.data_ptr(), st.cuda_stream)
         return perm, seg

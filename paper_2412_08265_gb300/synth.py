@@ -115,7 +115,8 @@ class Telescope:
     ``lsf_sigma`` Angstrom; a radius <= 0 means ceil(4 sigma). ``resample``
     0 takes each bin's value at its centre (linear interpolation), 1 the mean
     over the bin ``[lambda_j - dlambda/2, lambda_j + dlambda/2]``
-    (flux-conserving rebinning).
+    (flux-conserving rebinning). ``row_lo``, ``row_hi`` select a window of
+    spaxel rows to model (0, 0: all rows), as a row-sharded galaxy does.
     """
 
     nx: int
@@ -131,6 +132,8 @@ class Telescope:
     z_cosmo: float = 0.0
     flux_scale: float = 1.0
     resample: int = 0
+    row_lo: int = 0
+    row_hi: int = 0
 
 
 # --------------------------------------------------------------------------

@@ -1,6 +1,7 @@
-"""Multi-process host logic of the benchmark on CPU (gloo, world size 2):
-the whole-job aggregate over ranks, and a rank that fails before the
-collective ends the other rank's wait with an error instead of a hang.
+"""Multi-process host logic on CPU (gloo, world size 2): the benchmark's
+whole-job aggregate over ranks, a rank that fails before the collective ends
+the other rank's wait with an error instead of a hang, and the halo exchange
+of spaxel-row sharding.
 One process per rank, as under torchrun; no GPU is used."""
 import os
 import socket
@@ -55,6 +56,23 @@ def _one_rank_fails(rank, port, q):
         q.put((rank, "error:" + type(e).__name__))
 
 
+def _halo_exchange(rank, port, q):
+    sys.path.insert(0, ROOT)
+    from paper_2412_08265_gb300.shard import exchange_halos, halo_plan, row_blocks
+    _init(rank, port)
+    ny, nx, nl, h = 11, 3, 4, 3
+    blocks = row_blocks(ny, 2)
+    lo, hi = blocks[rank]
+    value = lambda r: torch.arange(nx * nl, dtype=torch.float32).reshape(nx, nl) + 1000.0 * r
+    own = torch.stack([value(r) for r in range(lo, hi)])
+    ext = exchange_halos(own, h, rank, 2)
+    b, a = halo_plan(blocks, h)[rank]
+    want = torch.stack([value(r) for r in range(lo - b, hi + a)])
+    q.put((rank, (lo, hi), (b, a), bool(torch.equal(ext, want))))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def _run(fn):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -81,3 +99,15 @@ def test_failed_rank_ends_the_collective_with_an_error():
     out, codes = _run(_one_rank_fails)
     assert out[1] == (1, "exit") and codes[1] == 3
     assert out[0][0] == 0 and out[0][1].startswith("error:")
+
+
+def test_row_shard_halo_exchange_two_ranks():
+    """Row sharding's exchange step: each rank ends with its own rows plus the
+    PSF-radius rows of its neighbour (none beyond the field's edges), and the
+    two blocks cover the field once."""
+    out, codes = _run(_halo_exchange)
+    assert codes == [0, 0]
+    (r0, blk0, halo0, ok0), (r1, blk1, halo1, ok1) = out
+    assert blk0 == (0, 5) and blk1 == (5, 11)
+    assert halo0 == (0, 3) and halo1 == (3, 0)
+    assert ok0 and ok1
