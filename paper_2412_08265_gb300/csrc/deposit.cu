@@ -107,15 +107,15 @@ int launch_setup(const SetupParams& P, long long n_total, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------------------------
-// Work items: one per <= chunk particles of a spaxel (all age bands); empty
-// spaxels get one empty item (its row is written as zeros).
+// Work items: one per <= chunk particles of a spaxel (all age bands). Empty
+// spaxels get no item: k_zero_empty writes their rows.
 // ----------------------------------------------------------------------------
 __global__ void k_item_counts(ItemParams P) {
     const int nb = P.n_bands;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= P.n_s; s += gridDim.x * blockDim.x) {
         if (s == P.n_s) { P.n_items[s] = 0; P.n_parts[s] = 0; continue; }
         const int cnt = P.seg_off[(long long)(s + 1) * nb] - P.seg_off[(long long)s * nb];
-        const int ni = cnt > 0 ? (cnt + P.chunk - 1) / P.chunk : 1;
+        const int ni = (cnt + P.chunk - 1) / P.chunk;
         P.n_items[s] = ni;
         P.n_parts[s] = ni > 1 ? ni : 0;
     }
@@ -662,6 +662,40 @@ int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, 
     k_job_cost<<<1, 32, 0, st>>>(P, P.job_cost);
     fn<<<n_ctas, threads, smem, st>>>(P, *tmap);
     return 2;  // job-cost prep + deposit
+}
+
+// ----------------------------------------------------------------------------
+// Rows of spaxels without particles: zeros (one warp per row, 16-byte stores
+// when the rows are 16-byte aligned). The deposit has no work item for them,
+// so a small galaxy in a large field costs the deposit only its own spaxels.
+// ----------------------------------------------------------------------------
+__global__ void k_zero_empty(const int* __restrict__ seg_off, int n_s, int nb, float* __restrict__ cube, int pitch,
+                             int n_lambda) {
+    const int lane = threadIdx.x & 31;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const bool vec = (pitch % 4) == 0 && (reinterpret_cast<uintptr_t>(cube) & 15) == 0;
+    for (long long s = w0; s < n_s; s += nw) {
+        if (seg_off[(s + 1) * nb] != seg_off[s * nb]) continue;
+        float* row = cube + s * pitch;
+        int j0 = 0;
+        if (vec) {
+            float4* r4 = reinterpret_cast<float4*>(row);
+            const int n4 = n_lambda >> 2;
+            for (int j = lane; j < n4; j += 32) r4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            j0 = n4 << 2;
+        }
+        for (int j = j0 + lane; j < n_lambda; j += 32) row[j] = 0.f;
+    }
+}
+
+int launch_zero_empty(const int* seg_off, int n_s, int nb, float* cube, int pitch, int n_lambda, cudaStream_t st) {
+    if (n_s <= 0) return 0;
+    long long nb_blocks = ((long long)n_s * 32 + 255) / 256;
+    const long long cap = 16ll * sm_count();
+    if (nb_blocks > cap) nb_blocks = cap;
+    k_zero_empty<<<(int)nb_blocks, 256, 0, st>>>(seg_off, n_s, nb, cube, pitch, n_lambda);
+    return 1;
 }
 
 // ----------------------------------------------------------------------------

@@ -776,8 +776,9 @@ int enqueue_deposit(const SspState& S, const DepJob* jobs, int n_jobs, long long
 
 int enqueue_post(Plan& P, float* target, float* out, uint64_t noise_seed, float noise_s2n, cudaStream_t st,
                  cudaEvent_t* ev) {
-    int l = launch_combine(P.d_part_off, P.n_s, P.tel.n_lambda, P.d_partials, target,
-                           target == P.d_cube0 ? P.pitch0 : P.tel.n_lambda, st);
+    const int pitch = target == P.d_cube0 ? P.pitch0 : P.tel.n_lambda;
+    int l = launch_zero_empty(P.d_seg_off, P.n_s, P.S->n_bands, target, pitch, P.tel.n_lambda, st);
+    l += launch_combine(P.d_part_off, P.n_s, P.tel.n_lambda, P.d_partials, target, pitch, st);
     if (ev) cudaEventRecord(ev[4], st);
     const bool noise = noise_s2n > 0.f;
     if (P.need_conv || noise) {

@@ -163,6 +163,9 @@ int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, 
                    cudaStream_t st);
 size_t deposit_smem_bytes(int ncb, int slab_w);
 
+// Zero rows of the spaxels without particles (no work item covers them).
+int launch_zero_empty(const int* seg_off, int n_s, int nb, float* cube, int pitch, int n_lambda, cudaStream_t st);
+
 // K5: combine partial rows of split spaxels in a fixed order: FP32 for at most
 // kCombineF32Rows rows, FP64 above.
 constexpr int kCombineF32Rows = 4;

@@ -84,6 +84,20 @@ def test_backward_mid_size_sampled(torch_cuda):
     _grad_check(torch_cuda, wl, G, sample=sample)
 
 
+def test_backward_quadratic_loss_mid_size(torch_cuda):
+    """The differentiable workload itself: 1e6 particles, 150x150x3721, loss
+    1/2 |cube - target|^2 with the target from ages and metallicities x (1 +
+    N(0, 0.1)) and velocities + 20 km/s; dL/dcube = cube - target from the
+    oracle; gradients of 100 sampled particles against the oracle's."""
+    wl = synth.mid_galaxy()
+    tgt = synth.perturbed_target(wl.particles)
+    cube = oracle.forward(wl.particles, wl.ssp, wl.telescope, n_threads=NT)
+    target = oracle.forward(tgt, wl.ssp, wl.telescope, n_threads=NT)
+    rng = np.random.default_rng(12)
+    sample = np.sort(rng.choice(wl.particles.n, 100, replace=False))
+    _grad_check(torch_cuda, wl, cube - target, sample=sample)
+
+
 def test_backward_bf16_templates(torch_cuda):
     wl = synth.small_galaxy(n=3000, seed=7)
     rng = np.random.default_rng(8)
