@@ -93,8 +93,8 @@ __device__ __noinline__ AdjSums adj_general(const float4 w, const float4 g4, con
             q0 = p[0];
             q1 = p[C.ncb];
         } else {
-            q0 = quad_global(quad, C.n_cells, C.n_ls, cell, k);
-            q1 = quad_global(quad, C.n_cells, C.n_ls, cell, k + 1);
+            q0 = quad_global(quad, C, cell, k);
+            q1 = quad_global(quad, C, cell, k + 1);
         }
         const float m0 = quad_dot(w, q0), m1 = quad_dot(w, q1);
         const float a0 = s01 * (q0.y - q0.x) + s23 * (q0.w - q0.z), a1 = s01 * (q1.y - q1.x) + s23 * (q1.w - q1.z);
@@ -196,7 +196,7 @@ __device__ __noinline__ AdjSums adj_mean_bin(const float4 w, const float4 wa, co
     const int ka = node_pos(j, bi, g4.y, g4.z, g4.w, fa);
     const int kb = node_pos(j + 1, bi, g4.y, g4.z, g4.w, fb);
     auto node = [&](int k) {
-        return use_slab ? slab[(k - C.klo) * C.ncb + (cell - C.cell0)] : quad_global(quad, C.n_cells, C.n_ls, cell, k);
+        return use_slab ? slab[(k - C.klo) * C.ncb + (cell - C.cell0)] : quad_global(quad, C, cell, k);
     };
     const float len = (float)(kb - ka) + (fb - fa);
     if (!(len > 0.f)) return S;
@@ -384,6 +384,8 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
     C.n_lambda = P.n_lambda;
     C.n_ls = P.n_ls;
     C.n_cells = P.n_cells;
+    C.q16 = P.quad16;
+    C.qdt = P.qdt;
     const uint32_t slab_bytes = (uint32_t)P.n_boxes * (uint32_t)P.box_w * (uint32_t)P.ncb * sizeof(float4);
     uint32_t phase = 0;
     const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(P.rec);
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
             __syncthreads();  // all warps are done with the previous slab
             if (threadIdx.x == 0) {
                 *s_next = 0;
-                if (C.slab_w > 0) {
+                if (C.slab_w > 0 && !C.qdt) {
                     fence_proxy_async_smem();
                     mbar_arrive_expect_tx(bar, slab_bytes);
                     for (int bx = 0; bx < P.n_boxes; ++bx)
@@ -411,9 +413,12 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
                 }
             }
             bool ok = true;
-            if (C.slab_w > 0) {
+            if (C.slab_w > 0 && !C.qdt) {
                 ok = mbar_wait_bounded(bar, phase, 4000000000ll);
                 phase ^= 1u;
+            } else if (C.slab_w > 0) {
+                // 16-bit templates: every thread converts part of the slab
+                fill_slab16(slab, C);
             }
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) atomicOr(P.err, kErrTmaTimeout);

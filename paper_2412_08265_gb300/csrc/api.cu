@@ -340,6 +340,8 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, uint64_t forward_ta
     launch_adjoint_setup(A, P.d_rec, P.d_wu, st);
     AdjTileParams T{};
     T.quad = S.d_quad;
+    T.quad16 = S.d_quad16;
+    T.qdt = S.qdt;
     T.n_cells = S.n_cells;
     T.n_ls = S.ssp.n_ls;
     T.rec = P.d_rec;

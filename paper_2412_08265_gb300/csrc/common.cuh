@@ -18,23 +18,6 @@ enum DeviceError : unsigned {
 };
 
 // ----------------------------------------------------------------------------
-// Template storage types
-// ----------------------------------------------------------------------------
-template <typename T> struct TplTraits;
-template <> struct TplTraits<float> {
-    static constexpr int kBytes = 4;
-    __device__ static __forceinline__ float ld(const float* p) { return *p; }
-};
-template <> struct TplTraits<__nv_bfloat16> {
-    static constexpr int kBytes = 2;
-    __device__ static __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-};
-template <> struct TplTraits<__half> {
-    static constexpr int kBytes = 2;
-    __device__ static __forceinline__ float ld(const __half* p) { return __half2float(*p); }
-};
-
-// ----------------------------------------------------------------------------
 // Shared-memory barrier and TMA (inline PTX, sm_90+ forms valid on sm_103a)
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {

@@ -186,8 +186,8 @@ __device__ __noinline__ float bin_value(const float4 w4, const float4 g4, const 
         q0 = p[0];
         q1 = p[C.ncb];
     } else {
-        q0 = quad_global(quad, C.n_cells, C.n_ls, cell, k);
-        q1 = quad_global(quad, C.n_cells, C.n_ls, cell, k + 1);
+        q0 = quad_global(quad, C, cell, k);
+        q1 = quad_global(quad, C, cell, k + 1);
     }
     const float m0 = quad_dot(w4, q0), m1 = quad_dot(w4, q1);
     return fmaf(f, m1 - m0, m0);
@@ -390,7 +390,7 @@ __device__ __noinline__ float mean_value(const float4 w4, const float4 g4, const
     const int kb = node_pos(j + 1, rec_bi(c0_bi), g4.y, g4.z, g4.w, fb);
     auto node = [&](int k) {
         const float4 q = use_slab ? slab[(k - C.klo) * C.ncb + (cell - C.cell0)]
-                                  : quad_global(quad, C.n_cells, C.n_ls, cell, k);
+                                  : quad_global(quad, C, cell, k);
         return quad_dot(w4, q);
     };
     // segments [k, k + 1] outside [-1, n_ls] are zero
@@ -529,6 +529,8 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_deposit(c
     C.n_lambda = P.n_lambda;
     C.n_ls = P.n_ls;
     C.n_cells = P.n_cells;
+    C.q16 = P.quad16;
+    C.qdt = P.qdt;
     const uint32_t slab_bytes = (uint32_t)P.n_boxes * (uint32_t)P.box_w * (uint32_t)P.ncb * sizeof(float4);
     uint32_t phase = 0;
 
@@ -567,7 +569,7 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_deposit(c
             __syncthreads();  // all warps are done with the previous slab and rows
             if (threadIdx.x == 0) {
                 *s_next = 0;
-                if (C.slab_w > 0) {
+                if (C.slab_w > 0 && !C.qdt) {
                     fence_proxy_async_smem();
                     mbar_arrive_expect_tx(bar, slab_bytes);
                     for (int bx = 0; bx < P.n_boxes; ++bx)
@@ -576,9 +578,12 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_deposit(c
                 }
             }
             bool ok = true;
-            if (C.slab_w > 0) {
+            if (C.slab_w > 0 && !C.qdt) {
                 ok = mbar_wait_bounded(bar, phase, 4000000000ll);
                 phase ^= 1u;
+            } else if (C.slab_w > 0) {
+                // 16-bit templates: every thread converts part of the slab
+                fill_slab16(slab, C);
             }
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) atomicOr(P.err, kErrTmaTimeout);

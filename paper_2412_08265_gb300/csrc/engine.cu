@@ -208,7 +208,7 @@ void ssp_state_destroy(SspState* S) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(S->device);
-    void* ptrs[] = {S->d_tpl, S->d_quad, S->d_la, S->d_lz, S->d_tile_klo, S->d_err, S->d_slow};
+    void* ptrs[] = {S->d_quad, S->d_quad16, S->d_la, S->d_lz, S->d_tile_klo, S->d_err, S->d_slow};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     cudaSetDevice(prev);
@@ -234,37 +234,17 @@ rubix_status ssp_state_create(const rubix_ssp_grid* ssp, const rubix_telescope* 
     h->dlambda = tel->dlambda;
     h->z_cosmo = tel->z_cosmo;
 
-    // ---- SSP grid to the device in its storage dtype, rows padded to 16 B ----
+    // ---- SSP grid: sizes and node vectors (the templates go to the device as
+    // cell quads, below) ----
     SspDev& S = h->ssp;
     S.dtype = ssp->storage_dtype;
-    h->elem = (S.dtype == RUBIX_F32) ? 4 : 2;
     S.n_age = ssp->n_age;
     S.n_Z = ssp->n_Z;
     S.n_t = ssp->n_age * ssp->n_Z;
     S.n_ls = ssp->n_lambda;
-    S.pitch = (ssp->n_lambda + 7) / 8 * 8;
     S.ls0 = ssp->lambda0;
     S.dls = ssp->dlambda;
     {
-        const size_t cnt = (size_t)S.n_t * S.pitch;
-        std::vector<unsigned char> host(cnt * h->elem, 0);
-        for (int c = 0; c < S.n_t; ++c)
-            for (int k = 0; k < S.n_ls; ++k) {
-                const float f = (float)ssp->spectra[(size_t)c * S.n_ls + k];
-                const size_t o = (size_t)c * S.pitch + k;
-                if (S.dtype == RUBIX_F32) {
-                    std::memcpy(&host[o * 4], &f, 4);
-                } else if (S.dtype == RUBIX_BF16) {
-                    const uint16_t b = f32_to_bf16(f);
-                    std::memcpy(&host[o * 2], &b, 2);
-                } else {
-                    const __half hv = __float2half_rn(f);
-                    std::memcpy(&host[o * 2], &hv, 2);
-                }
-            }
-        if (cudaMalloc(&h->d_tpl, host.size()) != cudaSuccess) return bail(fail(RUBIX_ERR_OOM, "SSP alloc"));
-        if (cudaMemcpy(h->d_tpl, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail(fail(RUBIX_ERR_CUDA, "SSP copy"));
         std::vector<float> la(S.n_age), lz(S.n_Z);
         for (int i = 0; i < S.n_age; ++i) la[i] = (float)ssp->log10_age_nodes[i];
         for (int i = 0; i < S.n_Z; ++i) lz[i] = (float)ssp->log10_Z_nodes[i];
@@ -275,41 +255,58 @@ rubix_status ssp_state_create(const rubix_ssp_grid* ssp, const rubix_telescope* 
         cudaMemcpy(h->d_lz, lz.data(), lz.size() * 4, cudaMemcpyHostToDevice);
         cudaMemset(h->d_err, 0, 16);
         cudaMemset(h->d_slow, 0, 8);
-        S.tpl = h->d_tpl;
         S.la_nodes = h->d_la;
         S.lz_nodes = h->d_lz;
     }
 
-    // ---- cell quads: for SSP cell (ia, iz) and node k, the float4 of its four
-    // bilinear corners (ia,iz) (ia+1,iz) (ia,iz+1) (ia+1,iz+1), in the storage
-    // dtype's values, node-major [n_ls][n_cells] ----
+    // ---- cell quads: for SSP cell (ia, iz) and node k, the four bilinear
+    // corners (ia,iz) (ia+1,iz) (ia,iz+1) (ia+1,iz+1), node-major
+    // [n_ls][n_cells], in the storage dtype: a float4 of FP32 values, or an
+    // 8-byte uint2 of BF16 / FP16 bit patterns (x = corner 0 | corner 1 << 16,
+    // y = corner 2 | corner 3 << 16) that the kernels widen to FP32 exactly ----
     h->cz = std::max(S.n_Z - 1, 1);
     const int ca = std::max(S.n_age - 1, 1);
     h->n_cells = ca * h->cz;
+    h->qdt = (S.dtype == RUBIX_F32) ? 0 : (S.dtype == RUBIX_BF16 ? 1 : 2);
     {
         const int da = (S.n_age > 1) ? 1 : 0, dz = (S.n_Z > 1) ? 1 : 0;
-        auto stored = [&](int ia, int iz, int k) {
-            const float f = (float)ssp->spectra[((size_t)ia * S.n_Z + iz) * S.n_ls + k];
-            if (S.dtype == RUBIX_F32) return f;
-            if (S.dtype == RUBIX_BF16) {
-                const uint32_t u = (uint32_t)f32_to_bf16(f) << 16;
-                float r;
-                std::memcpy(&r, &u, 4);
-                return r;
-            }
-            return __half2float(__float2half_rn(f));
+        auto tpl = [&](int ia, int iz, int k) { return (float)ssp->spectra[((size_t)ia * S.n_Z + iz) * S.n_ls + k]; };
+        auto bits16 = [&](float f) -> uint32_t {
+            if (S.dtype == RUBIX_BF16) return f32_to_bf16(f);
+            const __half hv = __float2half_rn(f);
+            uint16_t b;
+            std::memcpy(&b, &hv, 2);
+            return b;
         };
-        std::vector<float4> q((size_t)S.n_ls * h->n_cells);
-        for (int ia = 0; ia < ca; ++ia)
-            for (int iz = 0; iz < h->cz; ++iz) {
-                const int c = ia * h->cz + iz;
-                for (int k = 0; k < S.n_ls; ++k)
-                    q[(size_t)k * h->n_cells + c] = make_float4(stored(ia, iz, k), stored(ia + da, iz, k),
-                                                                stored(ia, iz + dz, k), stored(ia + da, iz + dz, k));
-            }
-        if (dalloc_sync(&h->d_quad, q.size())) return bail(fail(RUBIX_ERR_OOM, "quad alloc"));
-        if (cudaMemcpy(h->d_quad, q.data(), q.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail(fail(RUBIX_ERR_CUDA, "quad copy"));
+        const size_t nq = (size_t)S.n_ls * h->n_cells;
+        if (h->qdt == 0) {
+            std::vector<float4> q(nq);
+            for (int ia = 0; ia < ca; ++ia)
+                for (int iz = 0; iz < h->cz; ++iz) {
+                    const int c = ia * h->cz + iz;
+                    for (int k = 0; k < S.n_ls; ++k)
+                        q[(size_t)k * h->n_cells + c] = make_float4(tpl(ia, iz, k), tpl(ia + da, iz, k),
+                                                                    tpl(ia, iz + dz, k), tpl(ia + da, iz + dz, k));
+                }
+            if (dalloc_sync(&h->d_quad, q.size())) return bail(fail(RUBIX_ERR_OOM, "quad alloc"));
+            if (cudaMemcpy(h->d_quad, q.data(), q.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(RUBIX_ERR_CUDA, "quad copy"));
+        } else {
+            std::vector<uint2> q(nq);
+            for (int ia = 0; ia < ca; ++ia)
+                for (int iz = 0; iz < h->cz; ++iz) {
+                    const int c = ia * h->cz + iz;
+                    for (int k = 0; k < S.n_ls; ++k) {
+                        uint2 v;
+                        v.x = bits16(tpl(ia, iz, k)) | (bits16(tpl(ia + da, iz, k)) << 16);
+                        v.y = bits16(tpl(ia, iz + dz, k)) | (bits16(tpl(ia + da, iz + dz, k)) << 16);
+                        q[(size_t)k * h->n_cells + c] = v;
+                    }
+                }
+            if (dalloc_sync(&h->d_quad16, q.size())) return bail(fail(RUBIX_ERR_OOM, "quad alloc"));
+            if (cudaMemcpy(h->d_quad16, q.data(), q.size() * sizeof(uint2), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(RUBIX_ERR_CUDA, "quad copy"));
+        }
     }
 
     // ---- deposit tiling: wavelength tiles and the quad slab staged per tile
@@ -383,7 +380,7 @@ rubix_status ssp_state_create(const rubix_ssp_grid* ssp, const rubix_telescope* 
         return bail(fail(RUBIX_ERR_CUDA, "internal: TMA box of %d x %d quads is not 128-byte aligned", h->box_w, h->ncb));
     h->dep_smem = deposit_smem_bytes(h->ncb, h->slab_w);
     h->dep_ctas = h->n_sm * RUBIX_DEP_CTAS;
-    if (h->slab_w > 0) {
+    if (h->slab_w > 0 && h->qdt == 0) {
         PFN_encodeTiled_t enc = get_encode_tiled();
         if (!enc) return bail(fail(RUBIX_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"));
         // 2-D view of the quads: x = 4 floats per cell (innermost), y = node
@@ -753,6 +750,8 @@ int enqueue_deposit(const SspState& S, const DepJob* jobs, int n_jobs, long long
     if (n_jobs < 1 || n_jobs > kMaxJobs) return -1;
     DepositParams DP{};
     DP.quad = S.d_quad;
+    DP.quad16 = S.d_quad16;
+    DP.qdt = S.qdt;
     DP.n_cells = S.n_cells;
     DP.n_ls = S.ssp.n_ls;
     for (int j = 0; j < n_jobs; ++j) DP.jobs[j] = jobs[j];

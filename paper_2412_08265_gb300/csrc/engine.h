@@ -19,19 +19,19 @@ rubix_status fail(rubix_status st, const char* fmt, ...);
 void set_last_error(const char* msg);
 
 // SSP templates on one device + the deposit tiling for one output wavelength
-// grid (n_lambda, lambda0, dlambda, z_cosmo): the templates in their storage
-// dtype (setup, adjoint), the cell quads the deposit reads, wavelength tiles,
+// grid (n_lambda, lambda0, dlambda, z_cosmo): the cell quads the deposit and
+// adjoint read (the storage dtype's values), wavelength tiles,
 // the age bands and width of the shared-memory quad slab, and its TMA
 // descriptor.
 struct SspState {
     int device = 0, n_sm = 0, smem_optin = 0;
     SspDev ssp{};
-    void* d_tpl = nullptr;
-    float4* d_quad = nullptr;   // [n_ls][n_cells] cell quads, FP32
+    float4* d_quad = nullptr;   // [n_ls][n_cells] cell quads, FP32 templates
+    uint2* d_quad16 = nullptr;  // [n_ls][n_cells] cell quads, BF16 / FP16 templates (qdt 1 / 2)
+    int qdt = 0;
     int n_cells = 0, cz = 1;    // cells = max(n_age-1,1) * cz, cz = max(n_Z-1,1)
     float* d_la = nullptr;
     float* d_lz = nullptr;
-    int elem = 4;
     int n_lambda = 0;
     double lambda0 = 0, dlambda = 0, z_cosmo = 0;
     int tile_w = 31, n_tiles = 0, slab_w = 0, ncb = 1, box_w = 0, n_boxes = 0;

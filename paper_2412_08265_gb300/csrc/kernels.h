@@ -82,11 +82,10 @@ size_t sort_scratch_ints(long long n);
 int launch_sort_by_key(const int* keys, long long n, int n_keys, int* keys_tmp, int* vals_tmp, int* keys_out,
                        int* perm_out, int* seg_off, int* scratch, cudaStream_t st);
 
-// SSP grid as stored on the device.
+// SSP grid as seen by the kernels (the templates themselves as cell quads).
 struct SspDev {
-    const void* tpl;        // [n_t][pitch] in the storage dtype
     int dtype;              // 0 f32, 1 bf16, 2 f16
-    int n_age, n_Z, n_t, n_ls, pitch;
+    int n_age, n_Z, n_t, n_ls;
     const float* la_nodes;  // [n_age]
     const float* lz_nodes;  // [n_Z]
     double ls0, dls;
@@ -141,7 +140,9 @@ struct DepJob {
     int resample;            // 1: bin means (records hold the bins' lower edges)
 };
 struct DepositParams {
-    const float4* quad;      // [n_ls][n_cells] SSP cell quads (the four bilinear corners per node)
+    const float4* quad;      // [n_ls][n_cells] SSP cell quads (the four bilinear corners per node), FP32
+    const uint2* quad16;     // the same as 16-bit values (qdt 1: BF16, 2: FP16; quad is then null)
+    int qdt;
     int n_cells, n_ls;
     DepJob jobs[kMaxJobs];
     int n_jobs;
@@ -217,6 +218,8 @@ struct AdjointParams {
 // over the tile's bins (unit mass), from the same shared-memory quad slabs.
 struct AdjTileParams {
     const float4* quad;
+    const uint2* quad16;        // 16-bit quads (qdt 1: BF16, 2: FP16; quad is then null)
+    int qdt;
     int n_cells, n_ls;
     const DepRec* rec;          // [n_in] forward records (sorted order)
     const float4* wu;           // [n_in] unit-mass bilinear weights (0: spectrum misses every bin)

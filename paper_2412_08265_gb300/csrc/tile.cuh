@@ -35,12 +35,64 @@ __device__ __forceinline__ int node_pos(int j, int bi, float bf, float a_hi, flo
 
 struct TileCtx {
     int j0, klo, slab_w, ncb, cell0, n_lambda, n_ls, n_cells;
+    const uint2* q16;  // 16-bit cell quads (qdt 1: BF16, 2: FP16); null: FP32 quads
+    int qdt;
 };
 
-// Quad of `cell` at node k from the global quad array (zero outside the
-// template range: the template's zero extension).
-__device__ __forceinline__ float4 quad_global(const float4* __restrict__ quad, int n_cells, int n_ls, int cell, int k) {
-    return (k >= 0 && k < n_ls) ? __ldg(quad + (long long)k * n_cells + cell) : make_float4(0.f, 0.f, 0.f, 0.f);
+// The four corner templates of a 16-bit cell quad (x = corners 0 | 1 << 16,
+// y = corners 2 | 3 << 16) as FP32 values (exact).
+__device__ __forceinline__ float4 unpack_quad(const uint2 v, int qdt) {
+    if (qdt == 1)
+        return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u), __uint_as_float(v.y << 16),
+                           __uint_as_float(v.y & 0xffff0000u));
+    return make_float4(__half2float(__ushort_as_half((unsigned short)(v.x & 0xffffu))),
+                       __half2float(__ushort_as_half((unsigned short)(v.x >> 16))),
+                       __half2float(__ushort_as_half((unsigned short)(v.y & 0xffffu))),
+                       __half2float(__ushort_as_half((unsigned short)(v.y >> 16))));
+}
+
+// Quad of `cell` at node k from the global quad array, FP32 or 16-bit (zero
+// outside the template range: the template's zero extension).
+__device__ __forceinline__ float4 quad_global(const float4* __restrict__ quad, const TileCtx& C, int cell, int k) {
+    if (k < 0 || k >= C.n_ls) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long i = (long long)k * C.n_cells + cell;
+    return C.qdt ? unpack_quad(__ldg(C.q16 + i), C.qdt) : __ldg(quad + i);
+}
+
+// Slab of a (tile, band) from 16-bit quads, by all threads of the CTA: node
+// rows klo .. klo + slab_w of cells cell0 .. cell0 + ncb, converted to FP32
+// (zero outside the template range and past the last cell, as TMA's fill
+// does for FP32 quads). Thread i fills slab entries i, i + T, ... (T threads,
+// entry e = row e / ncb, cell e % ncb): consecutive threads read consecutive
+// cells of a node row and store consecutive 16-byte entries; kFill loads are
+// in flight per thread before their stores. The caller synchronises the CTA
+// afterwards.
+__device__ __forceinline__ void fill_slab16(float4* __restrict__ slab, const TileCtx& C) {
+    constexpr int kFill = 4;
+    const int T = blockDim.x, total = C.slab_w * C.ncb;
+    const int dr = T / C.ncb, dc = T - dr * C.ncb;
+    int r = threadIdx.x / C.ncb, c = threadIdx.x - r * C.ncb;
+    for (int e0 = threadIdx.x; e0 < total; e0 += kFill * T) {
+        uint2 v[kFill];
+        bool ok[kFill];
+#pragma unroll
+        for (int u = 0; u < kFill; ++u) {
+            const int k = C.klo + r, cell = C.cell0 + c;
+            ok[u] = e0 + u * T < total && k >= 0 && k < C.n_ls && cell < C.n_cells;
+            v[u] = ok[u] ? __ldg(C.q16 + (long long)k * C.n_cells + cell) : make_uint2(0u, 0u);
+            r += dr;
+            c += dc;
+            if (c >= C.ncb) {
+                c -= C.ncb;
+                ++r;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kFill; ++u) {
+            const int e = e0 + u * T;
+            if (e < total) slab[e] = ok[u] ? unpack_quad(v[u], C.qdt) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
 }
 
 // Mass-weighted bilinear template value at one node: sum_c w_c q_c.
