@@ -1,7 +1,7 @@
 // api.cu -- the C ABI of include/rubix.h for single-galaxy handles: a handle
 // is an SSP state (device templates + deposit tiling) and one plan (telescope
 // + device buffers); forward = pre (stage, keys, sort, setup, work items) ->
-// deposit (one job) -> post (FP64 combine, PSF/LSF/noise).
+// deposit (one job) -> post (combine of split spaxels, PSF/LSF/noise).
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -425,7 +425,7 @@ std::vector<Buf> plan_buffers(Plan* P, const SspState& S, int n_s, int n_lambda,
     const std::vector<Buf> rest = {
         {(void**)&P->d_key, 4 * N},
         {(void**)&P->d_keys_tmp, 4 * N}, {(void**)&P->d_vals_tmp, 4 * N}, {(void**)&P->d_skeys, 4 * N},
-        {(void**)&P->d_perm, 4 * N}, {(void**)&P->d_v, 8 * N},
+        {(void**)&P->d_perm, 4 * N}, {(void**)&P->d_pin, 16 * N},
         {(void**)&P->d_sort_scratch, 4 * sort_scratch_ints((long long)N)},
         {(void**)&P->d_items, sizeof(Item) * (size_t)item_cap}, {(void**)&P->d_rec, sizeof(DepRec) * N},
         {(void**)&P->d_prec, sizeof(PartRec) * N},
@@ -658,7 +658,7 @@ rubix_status enqueue_keys(Plan& P, const rubix_particles* p, int* keys_out, cuda
     if (s != RUBIX_OK) return s;
     AssignParams A = assign_params(P, p, arrs);
     A.key = keys_out;
-    A.v_out = nullptr;
+    A.pin_out = nullptr;
     launch_assign(A, st);
     CK(cudaGetLastError());
     return RUBIX_OK;
@@ -676,7 +676,9 @@ rubix_status enqueue_pre(Plan& P, const rubix_particles* p, cudaStream_t st, cud
     if (n > 0) {
         AssignParams A = assign_params(P, p, arrs);
         A.key = P.d_key;
-        A.v_out = P.d_v;
+        A.pin_out = P.d_pin;
+        A.mass = arrs[7];
+        A.Zm = arrs[9];
         A.dv_dang = P.d_dvda;  // null unless the plan keeps backward state
         A.age = arrs[8];
         A.la_nodes = S.d_la;
@@ -696,13 +698,13 @@ rubix_status enqueue_pre(Plan& P, const rubix_particles* p, cudaStream_t st, cud
     SP.seg_off = P.d_seg_off;
     SP.n_s = P.n_s;
     SP.n_bands = S.n_bands;
-    SP.mass = arrs[7];
-    SP.age = arrs[8];
-    SP.Z = arrs[9];
-    SP.v = P.d_v;
+    SP.pin = P.d_pin;
     SP.l0 = P.tel.lambda0;
     SP.dl = P.tel.dlambda;
     SP.z_cosmo = P.tel.z_cosmo;
+    SP.inv_c = 1.0 / kC_kms;
+    SP.alpha_z = 1.0 / ((1.0 + P.tel.z_cosmo) * S.ssp.dls);
+    SP.ls0_dls = S.ssp.ls0 / S.ssp.dls;
     SP.flux_scale = P.tel.flux_scale;
     SP.n_lambda = P.tel.n_lambda;
     SP.resample = P.tel.resample;
@@ -777,7 +779,9 @@ int enqueue_post(Plan& P, float* target, float* out, uint64_t noise_seed, float 
                  cudaEvent_t* ev) {
     const int pitch = target == P.d_cube0 ? P.pitch0 : P.tel.n_lambda;
     int l = launch_zero_empty(P.d_seg_off, P.n_s, P.S->n_bands, target, pitch, P.tel.n_lambda, st);
-    l += launch_combine(P.d_part_off, P.n_s, P.tel.n_lambda, P.d_partials, target, pitch, st);
+    // d_n_parts (scanned into d_part_off by the item stage) is free here: the
+    // combine's list of split spaxels
+    l += launch_combine(P.d_part_off, P.n_s, P.tel.n_lambda, P.d_partials, target, pitch, P.d_n_parts, st);
     if (ev) cudaEventRecord(ev[4], st);
     const bool noise = noise_s2n > 0.f;
     if (P.need_conv || noise) {

@@ -90,7 +90,7 @@ struct Plan {
           *d_vlos = nullptr;
     float *d_mass = nullptr, *d_age = nullptr, *d_Z = nullptr;
     int *d_key = nullptr, *d_keys_tmp = nullptr, *d_vals_tmp = nullptr, *d_skeys = nullptr, *d_perm = nullptr;
-    double* d_v = nullptr;
+    PartRec* d_pin = nullptr;  // [cap] (mass, age, Z, v_los) in original order, written by the assign
     int* d_sort_scratch = nullptr;
     int *d_seg_off = nullptr, *d_n_items = nullptr, *d_n_parts = nullptr, *d_item_off = nullptr;
     int *d_part_off = nullptr, *d_scan_scratch = nullptr;
@@ -127,7 +127,7 @@ void plan_release(Plan* P);                    // async plans: frees stream-orde
 
 // Forward in three enqueued parts (all on `st`): stage particles, assign keys,
 // sort, per-particle setup and work items; the (possibly batched) deposit; and
-// the FP64 combine + PSF/LSF/noise into `out`.
+// the combine of split spaxels + PSF/LSF/noise into `out`.
 // `ev` (optional, profiling): enqueue_pre records ev[1] after the sort,
 // enqueue_post records ev[4] after the combine.
 rubix_status enqueue_pre(Plan& P, const rubix_particles* p, cudaStream_t st, cudaEvent_t* ev = nullptr);

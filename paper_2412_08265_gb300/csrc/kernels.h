@@ -67,8 +67,12 @@ struct AssignParams {
     int nx, ny;
     int row_lo, rows; // row window: spaxel rows [row_lo, row_lo + rows) are kept (rows <= 0: all ny)
     int* key;         // [n]
-    double* v_out;    // [n] line-of-sight velocity (nullable)
-    // age bands (optional)
+    // [n] original order (nullable): (mass, age, Z, line-of-sight velocity),
+    // one 16-byte record per particle, so that the setup gathers one record
+    // per particle in sorted order instead of four arrays
+    PartRec* pin_out;
+    const float *mass, *Zm;
+    // age bands (optional; the age also goes into pin_out)
     const float* age;
     const float* la_nodes;
     int n_age, apb, n_bands;
@@ -97,9 +101,11 @@ struct SetupParams {
     const int* perm;         // sorted position -> particle index
     const int* seg_off;      // [n_s * n_bands + 2]
     int n_s, n_bands;
-    const float *mass, *age, *Z;
-    const double* v;         // line-of-sight velocity per particle
+    const PartRec* pin;      // [n] original order: (mass, age, Z, v_los) per particle
     double l0, dl, z_cosmo, flux_scale;
+    double inv_c;            // 1 / c in km/s
+    double alpha_z;          // 1 / ((1 + z_cosmo) dls)
+    double ls0_dls;          // ls0 / dls
     int n_lambda;
     int resample;            // 0: records map bin centres, 1: bin lower edges (bin means)
     DepRec* rec;             // [n_in]
@@ -168,10 +174,11 @@ size_t deposit_smem_bytes(int ncb, int slab_w);
 int launch_zero_empty(const int* seg_off, int n_s, int nb, float* cube, int pitch, int n_lambda, cudaStream_t st);
 
 // K5: combine partial rows of split spaxels in a fixed order: FP32 for at most
-// kCombineF32Rows rows, FP64 above.
+// kCombineF32Rows rows, a compensated FP32 sum (two-sum) above. list: n_s + 1
+// ints of scratch (the split spaxels and their count).
 constexpr int kCombineF32Rows = 4;
 int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube, int pitch,
-                   cudaStream_t st);
+                   int* list, cudaStream_t st);
 
 // K6: PSF + LSF (+ noise).
 constexpr int kMaxRadius = 64;

@@ -133,7 +133,7 @@ extern "C" rubix_status rubix_spaxel_sort_noalloc(const rubix_particles* p, cons
     A.nx = tel->nx;
     A.ny = tel->ny;
     A.key = keys;
-    A.v_out = nullptr;
+    A.pin_out = nullptr;
     launch_assign(A, st);
     launch_sort_by_key(keys, n, n_keys, keys_tmp, vals_tmp, skeys, perm_out, seg_off_out, sort_scratch, st);
     cudaError_t e = cudaGetLastError();

@@ -64,7 +64,14 @@ __global__ void k_assign(AssignParams P) {
             key = P.nx * rows * nb;
         }
         P.key[p] = key;
-        if (P.v_out) P.v_out[p] = v;
+        if (P.pin_out) {
+            PartRec r;
+            r.mass = P.mass[p];
+            r.age = P.age[p];
+            r.Z = P.Zm[p];
+            r.v = (float)v;
+            P.pin_out[p] = r;
+        }
     }
 }
 
@@ -189,18 +196,34 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int* __restri
     for (int d = threadIdx.x; d < nb; d += blockDim.x) counts[(long long)d * n_tiles + blockIdx.x] = hist[d];
 }
 
+// Scatter of one tile: each warp ranks its keys in index order (match.any),
+// the tile's keys are then placed in shared memory in (digit, index) order,
+// and written out from there, so that consecutive threads write consecutive
+// positions of a digit's run: the writes are coalesced runs instead of one
+// scattered 4-byte write per key. The output positions are those of the
+// per-key scatter (tile offset of the digit + keys of that digit before it in
+// the tile): the sort is stable and its result does not depend on this
+// staging.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const int* __restrict__ keys_in,
                                                                 const int* __restrict__ vals_in, long long n,
                                                                 int shift, int nbits, int n_tiles,
                                                                 const int* __restrict__ offsets,
                                                                 int* __restrict__ keys_out,
                                                                 int* __restrict__ vals_out) {
-    __shared__ int wcnt[kSortWarps][kMaxBuckets];
+    // wcnt is dead once the local positions are known: the staged keys reuse it
+    __shared__ int wcnt[kSortWarps][kMaxBuckets];  // 16 KB = kSortTile ints
+    __shared__ int s_val[kSortTile];
+    __shared__ int s_dig0[kMaxBuckets];   // first local position of digit d
+    __shared__ int s_goff[kMaxBuckets];   // the tile's global offset of digit d
+    __shared__ int s_wsum[kSortWarps];
+    static_assert(kSortWarps * kMaxBuckets >= kSortTile, "staging area");
+    int* s_key = &wcnt[0][0];
     const int nb = 1 << nbits, mask = nb - 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < nb; d += 32) wcnt[w][d] = 0;
     __syncwarp();
-    const long long base = (long long)blockIdx.x * kSortTile + (long long)w * (kSortTile / kSortWarps);
+    const long long tile0 = (long long)blockIdx.x * kSortTile;
+    const long long base = tile0 + (long long)w * (kSortTile / kSortWarps);
     const unsigned lt = (1u << lane) - 1u;
     int key[kSortRounds], rank[kSortRounds];
 #pragma unroll
@@ -219,25 +242,65 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const int* __res
         rank[r] = before + __popc(peers & lt);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < nb; d += blockDim.x) {
-        int run = 0;
+    // per digit: the warps' exclusive prefix (in place) and the tile's count;
+    // then the exclusive prefix of the counts over digits (two digits per thread)
+    int cnt2[2] = {0, 0};
 #pragma unroll
-        for (int ww = 0; ww < kSortWarps; ++ww) {
-            int t = wcnt[ww][d];
-            wcnt[ww][d] = run;
-            run += t;
+    for (int h = 0; h < 2; ++h) {
+        const int d = 2 * threadIdx.x + h;
+        if (d < nb) {
+            int run = 0;
+#pragma unroll
+            for (int ww = 0; ww < kSortWarps; ++ww) {
+                int t = wcnt[ww][d];
+                wcnt[ww][d] = run;
+                run += t;
+            }
+            cnt2[h] = run;
+            s_goff[d] = offsets[(long long)d * n_tiles + blockIdx.x];
+        }
+    }
+    int incl = cnt2[0] + cnt2[1];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_wsum[w] = incl;
+    __syncthreads();
+    int wpre = 0;
+#pragma unroll
+    for (int ww = 0; ww < kSortWarps; ++ww) wpre += (ww < w) ? s_wsum[ww] : 0;
+    const int excl = wpre + incl - (cnt2[0] + cnt2[1]);
+    if (2 * threadIdx.x < nb) s_dig0[2 * threadIdx.x] = excl;
+    if (2 * threadIdx.x + 1 < nb) s_dig0[2 * threadIdx.x + 1] = excl + cnt2[0];
+    __syncthreads();
+    // local positions (wcnt still holds the warps' prefixes), then stage
+    int lpos[kSortRounds];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const long long idx = base + r * 32 + lane;
+        const int d = (key[r] >> shift) & mask;
+        lpos[r] = (idx < n) ? s_dig0[d] + wcnt[w][d] + rank[r] : -1;
+    }
+    __syncthreads();  // every warp is done with wcnt
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        if (lpos[r] >= 0) {
+            const long long idx = base + r * 32 + lane;
+            s_key[lpos[r]] = key[r];
+            s_val[lpos[r]] = vals_in ? vals_in[idx] : (int)idx;
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kSortRounds; ++r) {
-        long long idx = base + r * 32 + lane;
-        if (idx < n) {
-            int d = (key[r] >> shift) & mask;
-            long long pos = (long long)offsets[(long long)d * n_tiles + blockIdx.x] + wcnt[w][d] + rank[r];
-            keys_out[pos] = key[r];
-            vals_out[pos] = vals_in ? vals_in[idx] : (int)idx;
-        }
+    const long long rem = n - tile0;
+    const int n_valid = rem < kSortTile ? (int)rem : kSortTile;
+    for (int i = threadIdx.x; i < n_valid; i += kSortThreads) {
+        const int k = s_key[i];
+        const int d = (k >> shift) & mask;
+        const long long pos = (long long)s_goff[d] + (i - s_dig0[d]);
+        keys_out[pos] = k;
+        vals_out[pos] = s_val[i];
     }
 }
 

@@ -299,8 +299,8 @@ def test_empty_outside_and_single(torch_cuda):
 @pytest.mark.parametrize("n", [600, 1024, 1025, 5000])
 def test_heavy_spaxel_split_combine(torch_cuda, n):
     """More than one work item of particles in a single spaxel: the split items'
-    rows are combined in FP32 for up to 4 items (600, 1024 particles) and in
-    FP64 above (1025, 5000)."""
+    rows are combined in FP32 for up to 4 items (600, 1024 particles) and with
+    a compensated FP32 sum above (1025, 5000)."""
     wl = synth.small_galaxy()
     rng = np.random.default_rng(4)
     f = lambda a: np.asarray(a, dtype=np.float32)
