@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "librubix.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "engine.cu", "serve.cu", "sort.cu", "deposit.cu", "psf_lsf.cu", "adjoint.cu", "adjoint_tiles.cu", "noalloc.cu", "selftest.cu", "peak.cu"]
+SOURCES = ["api.cu", "engine.cu", "serve.cu", "sort.cu", "setup.cu", "deposit.cu", "rows.cu", "psf_lsf.cu", "adjoint.cu", "adjoint_tiles.cu", "noalloc.cu", "selftest.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Host code is compiled without floating-point contraction: the orientation
 # matrix and the key coordinates are defined with every product and sum

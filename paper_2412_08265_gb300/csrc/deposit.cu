@@ -3,15 +3,17 @@
 // metallicity, shifted by its line-of-sight velocity, resampled onto the
 // instrument's wavelength grid and added to the spaxel it falls in).
 //
-// K3 (k_setup) turns each in-field particle, in sorted order, into a 32-byte
-// record: its four mass-scaled bilinear corner weights, its SSP cell (the
-// (ia, iz) cell whose four corner templates it interpolates) and the affine
-// map t(j) = B + jA from output bin j to the fractional SSP node position.
+// K3 (k_setup, setup.cu) has turned each in-field particle, in sorted order,
+// into a 32-byte record: its four mass-scaled bilinear corner weights, its
+// SSP cell (the (ia, iz) cell whose four corner templates it interpolates)
+// and the affine map t(j) = B + jA from output bin j to the fractional SSP
+// node position.
 //
 // The templates are kept, for the deposit, as cell quads: for SSP cell c and
-// node k, the float4 of its four corner templates at k, stored node-major
-// ([node][cell]) so that one 2-D TMA box holds a run of consecutive cells (an
-// age band) over a run of nodes.
+// node k, its four corner templates at k, stored node-major ([node][cell]) so
+// that one 2-D TMA box holds a run of consecutive cells (an age band) over a
+// run of nodes (FP32 quads; 16-bit quads are widened into the slab by the
+// CTA's threads).
 //
 // K4 (k_deposit) is persistent: each CTA owns a contiguous, cost-balanced range
 // of (wavelength tile, work item) pairs, a work item being <= chunk particles
@@ -35,128 +37,14 @@
 // the slab's halo, take a per-bin path.
 //
 // Spaxels with more than `chunk` particles are split into several items whose
-// FP32 partial rows K5 adds in item order (in FP64 for spaxels of many items),
-// so the cube is bitwise reproducible and no global atomics are used.
+// FP32 partial rows K5 (rows.cu) adds in item order, so the cube is bitwise
+// reproducible; later age bands add into the rows by L2 reductions in band
+// order (one per address and band, bands separated by the CTA barrier).
 #include "common.cuh"
 #include "kernels.h"
 #include "tile.cuh"
 
 namespace rubix {
-
-// ----------------------------------------------------------------------------
-// K3: per-particle setup (sorted order).
-// ----------------------------------------------------------------------------
-__global__ void k_setup(SetupParams P) {
-    const long long n_in = P.seg_off[(long long)P.n_s * P.n_bands];
-    if (n_in > P.n_cap) return;
-    const int n_ls = P.ssp.n_ls;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_in;
-         i += (long long)gridDim.x * blockDim.x) {
-        const PartRec pr = P.pin[P.perm[i]];
-        const float m = pr.mass, age = pr.age, Z = pr.Z;
-        const double v = (double)pr.v;
-        int ia, iz;
-        float ta, tz, dta, dtz;
-        ssp_cell(log10f(age), P.ssp.la_nodes, P.ssp.n_age, ia, ta, dta);
-        ssp_cell(log10f(Z), P.ssp.lz_nodes, P.ssp.n_Z, iz, tz, dtz);
-        const float ms = (float)P.flux_scale * m;
-        DepRec r;
-        r.w[0] = ms * ((1.f - ta) * (1.f - tz));
-        r.w[1] = ms * (ta * (1.f - tz));
-        r.w[2] = ms * ((1.f - ta) * tz);
-        r.w[3] = ms * (ta * tz);
-        const int c0 = ia * max(P.ssp.n_Z - 1, 1) + iz;  // SSP cell of the four corners
-        // t(j) = ((l0 + j dl) / dop - ls0) / dls = B + j A   (FP64), with
-        // dop = (1 + z)(1 + v/c): alpha = 1 / (dop dls) = alpha_z / (1 + v/c),
-        // alpha_z = 1 / ((1 + z) dls) and ls0 / dls from the host. The one
-        // reciprocal per particle is the FP32 reciprocal refined by one
-        // Newton-Raphson step in FP64, r0 (2 - q r0): the error squares,
-        // from 2^-24 to about 2^-48 relative -- 1e-11 node units over 3721
-        // nodes, far below the FP32 deposit's resolution -- on GB300's FP64
-        // pipe (1/64 of the FP32 rate) at a fraction of a correctly rounded
-        // division's cost.
-        const double q = 1.0 + v * P.inv_c;
-        const double r0 = (double)__frcp_rn((float)q);
-        const double rq = r0 * fma(-q, r0, 2.0);
-        const double alpha = P.alpha_z * rq;
-        // bin means: the record maps j to bin j's lower edge, t(j) - A/2,
-        // and the edges run j = 0 .. n_lambda
-        const double A = P.dl * alpha;
-        const double B = fma(P.l0, alpha, -P.ls0_dls) - (P.resample ? 0.5 * A : 0.0);
-        const double t_last = fma(A, (double)(P.resample ? P.n_lambda : P.n_lambda - 1), B);
-        int bi = 0;
-        float bf = 0.f, a_hi = 0.f, a_lo = 0.f;
-        if (!(q > 0.0) || !(B < (double)n_ls) || !(t_last >= -1.0) || !(B > -32768.0)) {
-            // the spectrum misses every output bin (a_hi = 0 marks the record)
-            r.w[0] = r.w[1] = r.w[2] = r.w[3] = 0.f;
-        } else {
-            const double fb = floor(B);
-            bi = (int)fb;
-            bf = (float)(B - fb);
-            const double ah = __longlong_as_double(__double_as_longlong(A) & ~((1ll << 42) - 1));
-            a_hi = (float)ah;
-            a_lo = (float)(A - ah);
-        }
-        r.c0_bi = (c0 << 16) | (bi & 0xffff);
-        r.bf = bf;
-        r.a_hi = a_hi;
-        r.a_lo = a_lo;
-        P.rec[i] = r;
-        P.prec[i] = pr;
-    }
-}
-
-int launch_setup(const SetupParams& P, long long n_total, cudaStream_t st) {
-    if (n_total <= 0) return 0;
-    long long nb = (n_total + 255) / 256;
-    if (nb > 16ll * sm_count()) nb = 16ll * sm_count();
-    k_setup<<<(int)nb, 256, 0, st>>>(P);
-    return 1;
-}
-
-// ----------------------------------------------------------------------------
-// Work items: one per <= chunk particles of a spaxel (all age bands). Empty
-// spaxels get no item: k_zero_empty writes their rows.
-// ----------------------------------------------------------------------------
-__global__ void k_item_counts(ItemParams P) {
-    const int nb = P.n_bands;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= P.n_s; s += gridDim.x * blockDim.x) {
-        if (s == P.n_s) { P.n_items[s] = 0; P.n_parts[s] = 0; continue; }
-        const int cnt = P.seg_off[(long long)(s + 1) * nb] - P.seg_off[(long long)s * nb];
-        const int ni = (cnt + P.chunk - 1) / P.chunk;
-        P.n_items[s] = ni;
-        P.n_parts[s] = ni > 1 ? ni : 0;
-    }
-}
-
-__global__ void k_item_fill(ItemParams P) {
-    const int nb = P.n_bands;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.n_s; s += gridDim.x * blockDim.x) {
-        const int base = P.item_off[s], ni = P.item_off[s + 1] - base;
-        const bool split = P.part_off[s + 1] > P.part_off[s];
-        const int b0 = P.seg_off[(long long)s * nb], e0 = P.seg_off[(long long)(s + 1) * nb];
-        for (int i = 0; i < ni; ++i) {
-            if ((long long)base + i >= P.item_cap) { atomicOr(P.err, kErrBadItem); return; }
-            Item it;
-            it.spaxel = s;
-            it.begin = b0 + i * P.chunk;
-            it.end = min(b0 + (i + 1) * P.chunk, e0);
-            it.part_row = split ? P.part_off[s] + i : -1;
-            P.items[base + i] = it;
-        }
-    }
-}
-
-int launch_items(const ItemParams& P, cudaStream_t st) {
-    int nb = (P.n_s + 1 + 255) / 256;
-    if (nb > 4096) nb = 4096;
-    k_item_counts<<<nb, 256, 0, st>>>(P);
-    int l = 1;
-    l += launch_exclusive_scan(P.n_items, P.item_off, P.n_s + 1, P.scan_scratch, st);
-    l += launch_exclusive_scan(P.n_parts, P.part_off, P.n_s + 1, P.scan_scratch, st);
-    k_item_fill<<<nb, 256, 0, st>>>(P);
-    return l + 1;
-}
 
 // ----------------------------------------------------------------------------
 // K4: deposit.
@@ -675,130 +563,6 @@ int launch_deposit(const DepositParams& P, const CUtensorMap* tmap, int n_ctas, 
     k_job_cost<<<1, 32, 0, st>>>(P, P.job_cost);
     fn<<<n_ctas, threads, smem, st>>>(P, *tmap);
     return 2;  // job-cost prep + deposit
-}
-
-// ----------------------------------------------------------------------------
-// Rows of spaxels without particles: zeros (one warp per row, 16-byte stores
-// when the rows are 16-byte aligned). The deposit has no work item for them,
-// so a small galaxy in a large field costs the deposit only its own spaxels.
-// ----------------------------------------------------------------------------
-__global__ void k_zero_empty(const int* __restrict__ seg_off, int n_s, int nb, float* __restrict__ cube, int pitch,
-                             int n_lambda) {
-    const int lane = threadIdx.x & 31;
-    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const bool vec = (pitch % 4) == 0 && (reinterpret_cast<uintptr_t>(cube) & 15) == 0;
-    for (long long s = w0; s < n_s; s += nw) {
-        if (seg_off[(s + 1) * nb] != seg_off[s * nb]) continue;
-        float* row = cube + s * pitch;
-        int j0 = 0;
-        if (vec) {
-            float4* r4 = reinterpret_cast<float4*>(row);
-            const int n4 = n_lambda >> 2;
-            for (int j = lane; j < n4; j += 32) r4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            j0 = n4 << 2;
-        }
-        for (int j = j0 + lane; j < n_lambda; j += 32) row[j] = 0.f;
-    }
-}
-
-int launch_zero_empty(const int* seg_off, int n_s, int nb, float* cube, int pitch, int n_lambda, cudaStream_t st) {
-    if (n_s <= 0) return 0;
-    long long nb_blocks = ((long long)n_s * 32 + 255) / 256;
-    const long long cap = 16ll * sm_count();
-    if (nb_blocks > cap) nb_blocks = cap;
-    k_zero_empty<<<(int)nb_blocks, 256, 0, st>>>(seg_off, n_s, nb, cube, pitch, n_lambda);
-    return 1;
-}
-
-// ----------------------------------------------------------------------------
-// K5: rows of split spaxels = the sum of their partial rows in item order: a
-// plain FP32 sum for spaxels of at most kCombineF32Rows items, a compensated
-// FP32 sum above (very high-count spaxels). The compensated sum carries the
-// rounding error of every addition (Knuth's two-sum: s + e is exactly the
-// sum of s and x) in a second FP32 accumulator: the error before the final
-// rounding stays within about n^2 2^-48 of the rows' magnitudes, far below
-// one FP32 rounding, as with an FP64 accumulator, without the FP64 pipe,
-// which on this GPU runs at 1/64 of the FP32 rate.
-// ----------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum_add(float& s, float& c, float x) {
-    const float t = s + x;
-    const float z = t - s;
-    c += (s - (t - z)) + (x - z);
-    s = t;
-}
-
-// The split spaxels, compacted (in any order: each row's sum is in item order,
-// so the result does not depend on it); list[n_s] counts them.
-__global__ void k_split_list(const int* __restrict__ part_off, int n_s, int* __restrict__ list) {
-    const int lane = threadIdx.x & 31;
-    for (int s0 = blockIdx.x * blockDim.x; s0 < n_s; s0 += gridDim.x * blockDim.x) {
-        const int s = s0 + threadIdx.x;
-        const bool split = s < n_s && part_off[s + 1] > part_off[s];
-        const unsigned m = __ballot_sync(0xffffffffu, split);
-        int at = 0;
-        if (lane == 0 && m) at = atomicAdd(list + n_s, __popc(m));
-        at = __shfl_sync(0xffffffffu, at, 0);
-        if (split) list[at + __popc(m & ((1u << lane) - 1u))] = s;
-    }
-}
-
-constexpr int kCombineBins = 128;  // bins of one row per combine unit: 4 per lane of one warp
-
-// One unit = kCombineBins bins of one split spaxel's row, taken by one warp
-// (lane l sums bins l, l + 32, l + 64, l + 96 of the unit: four independent
-// loads per partial row in flight), so that the rows of a very high-count
-// spaxel are summed by many warps at once and each warp has several loads
-// in flight while it waits on the next unit's row offsets.
-__global__ void __launch_bounds__(256) k_combine(const int* __restrict__ part_off, int n_s, int n_lambda,
-                                                 const int* __restrict__ list, const float* __restrict__ partials,
-                                                 float* __restrict__ cube, int pitch) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const int n_split = list[n_s];
-    const int n_chunks = (n_lambda + kCombineBins - 1) / kCombineBins;
-    const long long n_units = (long long)n_split * n_chunks;
-    for (long long u = warp; u < n_units; u += n_warps) {
-        const int s = list[u / n_chunks];
-        const int j0 = (int)(u % n_chunks) * kCombineBins + lane;
-        const int p0 = part_off[s], nr = part_off[s + 1] - p0;
-        const float* __restrict__ col = partials + (long long)p0 * n_lambda;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f}, err[4] = {0.f, 0.f, 0.f, 0.f};
-        bool in[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) in[k] = j0 + 32 * k < n_lambda;
-        if (nr <= kCombineF32Rows) {
-            // a few partial rows: FP32 adds lose nothing that the FP32 partial
-            // sums have not already lost
-            for (int r = 0; r < nr; ++r)
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (in[k]) acc[k] += col[(long long)r * n_lambda + j0 + 32 * k];
-        } else {
-#pragma unroll 2
-            for (int r = 0; r < nr; ++r)
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (in[k]) two_sum_add(acc[k], err[k], col[(long long)r * n_lambda + j0 + 32 * k]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[k] += err[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (in[k]) cube[(long long)s * pitch + j0 + 32 * k] = acc[k];
-    }
-}
-
-int launch_combine(const int* part_off, int n_s, int n_lambda, const float* partials, float* cube, int pitch,
-                   int* list, cudaStream_t st) {
-    if (n_s < 1) return 0;
-    cudaMemsetAsync(list + n_s, 0, sizeof(int), st);  // an error here is the caller's next cudaGetLastError
-    long long nb = ((long long)n_s + 255) / 256;
-    if (nb > 4ll * sm_count()) nb = 4ll * sm_count();
-    k_split_list<<<(int)nb, 256, 0, st>>>(part_off, n_s, list);
-    k_combine<<<8 * sm_count(), 256, 0, st>>>(part_off, n_s, n_lambda, list, partials, cube, pitch);
-    return 2;
 }
 
 }  // namespace rubix
