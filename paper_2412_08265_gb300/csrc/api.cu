@@ -293,6 +293,7 @@ extern "C" rubix_status rubix_cube_forward_tag(rubix_cube_t* h, uint64_t* tag) {
 extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, uint64_t forward_tag, const float* dL_dcube,
                                             float* d_mass, float* d_age, float* d_Z, float* d_vlos,
                                             double* d_global, void* stream) {
+    NvtxRange nvtx("rubix: backward");
     if (!h || !dL_dcube) return fail(RUBIX_ERR_INVALID_ARG, "NULL argument");
     const SspState& S = *h->S;
     Plan& P = h->P;

@@ -665,6 +665,7 @@ rubix_status enqueue_keys(Plan& P, const rubix_particles* p, int* keys_out, cuda
 }
 
 rubix_status enqueue_pre(Plan& P, const rubix_particles* p, cudaStream_t st, cudaEvent_t* ev) {
+    NvtxRange nvtx("rubix: assign, sort, setup, items");
     const SspState& S = *P.S;
     if (p->n > P.cap) return fail(RUBIX_ERR_INVALID_ARG, "more particles than the plan holds");
     const long long n = p->n;
@@ -749,6 +750,7 @@ DepJob plan_job(const Plan& P, float* target) {
 }
 
 int enqueue_deposit(const SspState& S, const DepJob* jobs, int n_jobs, long long* d_job_cost, cudaStream_t st) {
+    NvtxRange nvtx("rubix: deposit");
     if (n_jobs < 1 || n_jobs > kMaxJobs) return -1;
     DepositParams DP{};
     DP.quad = S.d_quad;
@@ -777,6 +779,7 @@ int enqueue_deposit(const SspState& S, const DepJob* jobs, int n_jobs, long long
 
 int enqueue_post(Plan& P, float* target, float* out, uint64_t noise_seed, float noise_s2n, cudaStream_t st,
                  cudaEvent_t* ev) {
+    NvtxRange nvtx("rubix: rows, PSF/LSF, noise");
     const int pitch = target == P.d_cube0 ? P.pitch0 : P.tel.n_lambda;
     int l = launch_zero_empty(P.d_seg_off, P.n_s, P.S->n_bands, target, pitch, P.tel.n_lambda, st);
     // d_n_parts (scanned into d_part_off by the item stage) is free here: the

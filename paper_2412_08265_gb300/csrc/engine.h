@@ -7,11 +7,22 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rubix.h"
 #include "common.cuh"
 #include "kernels.h"
 
 namespace rubix {
+
+// NVTX range over a host stage (enqueue time; a profiler that records NVTX
+// shows the stages of a forward, backward or serving batch by name).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Thread-local message behind rubix_last_error_message(); fail() sets it and
 // returns `st`.

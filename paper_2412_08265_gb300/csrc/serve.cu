@@ -175,6 +175,7 @@ int launches_in_flight(rubix_server* srv) {
 // One shared deposit launch for the ready requests, then each one's post stage.
 bool launch_batch(rubix_server* srv) {
     if (srv->ready.empty() || launches_in_flight(srv) > 1) return false;
+    NvtxRange nvtx("rubix: serving batch");
     Batch* B = nullptr;
     for (Batch& b : srv->batch_ev)
         if (!b.busy) {
