@@ -351,8 +351,10 @@ rubix_status ssp_state_create(const rubix_ssp_grid* ssp, const rubix_telescope* 
         if (cost < best.cost) best = Geo{apb, bands, ncb, box_w, n_boxes, slab_w, R, cost};
     }
     if (best.R == 0) {
-        // no slab fits (very wide Doppler halo): global-memory path only
-        best = Geo{ca, 1, 1, 0, 0, 0, 1, 0.0};
+        // no slab fits (very wide Doppler halo): global-memory path only. ncb
+        // = 0 fails every kernel's "cell inside the slab" test, so that no
+        // particle takes a fast path into the (absent) slab.
+        best = Geo{ca, 1, 0, 0, 0, 0, 1, 0.0};
     }
     h->apb = best.apb;
     h->n_bands = best.bands;
