@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
                 if (threadIdx.x == 0) atomicOr(P.err, kErrTmaTimeout);
                 return;
             }
-            constexpr int GR = RUBIX_DEP_GRAB;
+            constexpr int GR = RUBIX_ADJ_GRAB;
             while (true) {
                 int v0 = 0;
                 if (lane == 0) v0 = atomicAdd(s_next, GR);
@@ -445,6 +445,11 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
                             qe = min(qe, P.seg_off[(long long)sp * nb + band + 1]);
                         }
                         live = qb < qe;
+                        // the item's first weights and record, on their way to L1
+                        if (live) {
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(P.wu + qb));
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * qb + 1));
+                        }
                     }
                 }
                 unsigned m = __ballot_sync(0xffffffffu, live);

@@ -514,6 +514,9 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_deposit(c
                         }
                         // band 0 visits every item: it writes the row, zeros included
                         live = band == 0 || qb < qe;
+                        // the item's first record, on its way to L1 before the warp reaches it
+                        if (qb < qe)
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const float4*>(J.rec) + 2 * qb));
                     }
                 }
                 unsigned m = __ballot_sync(0xffffffffu, live);

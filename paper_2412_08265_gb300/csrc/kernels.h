@@ -48,9 +48,13 @@ int sm_count();
 #ifndef RUBIX_DEP_COSTC0
 #define RUBIX_DEP_COSTC0 4
 #endif
-// Work items a warp claims at once (its first lanes look them up together).
+// Work items a warp claims at once (its first lanes look them up together),
+// in the deposit and in the adjoint.
 #ifndef RUBIX_DEP_GRAB
 #define RUBIX_DEP_GRAB 4
+#endif
+#ifndef RUBIX_ADJ_GRAB
+#define RUBIX_ADJ_GRAB 4
 #endif
 
 // K1 parameters. The sort key is spaxel * n_bands + age band (n_bands <= 1:
