@@ -351,7 +351,7 @@ __device__ __forceinline__ AdjSums adj_mean_particle(const float4 w, const float
 }
 
 template <int R, bool MEAN>
-__global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_adjoint_tiles(const __grid_constant__ AdjTileParams P,
+__global__ void __launch_bounds__(RUBIX_ADJ_THREADS, RUBIX_DEP_CTAS) k_adjoint_tiles(const __grid_constant__ AdjTileParams P,
                                                                          const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);

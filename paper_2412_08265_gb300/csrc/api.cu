@@ -311,8 +311,17 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, uint64_t forward_ta
         // the PSF and LSF kernels are symmetric: their adjoint is the same convolution
         ConvParams C = P.conv;
         C.noise_inv_s2n = 0.f;
-        if (launch_psf_lsf(C, dL_dcube, P.tel.n_lambda, nullptr, P.d_tmp, P.d_cube0, st) < 0)
-            return fail(RUBIX_ERR_CUDA, "PSF/LSF transpose launch failed");
+        int lc;
+        if (P.has_grad_map) {
+            // the gradient into pitched rows, then the TMA kernel, as in the forward
+            CK(cudaMemcpy2DAsync(P.d_tmp, (size_t)P.pitch0 * sizeof(float), dL_dcube,
+                                 (size_t)P.tel.n_lambda * sizeof(float), (size_t)P.tel.n_lambda * sizeof(float),
+                                 (size_t)P.n_s, cudaMemcpyDeviceToDevice, st));
+            lc = launch_psf_lsf(C, P.d_tmp, P.pitch0, &P.grad_map, nullptr, P.d_cube0, st);
+        } else {
+            lc = launch_psf_lsf(C, dL_dcube, P.tel.n_lambda, nullptr, P.d_tmp, P.d_cube0, st);
+        }
+        if (lc < 0) return fail(RUBIX_ERR_CUDA, "PSF/LSF transpose launch failed");
         G0 = P.d_cube0;
     }
     launch_zero_grads(d_mass, d_age, d_Z, d_vlos, P.last_n, st);
@@ -368,7 +377,7 @@ extern "C" rubix_status rubix_cube_backward(rubix_cube_t* h, uint64_t forward_ta
     T.ls0_over = (float)(S.ssp.ls0 / S.ssp.dls);
     T.resample = P.tel.resample;
     T.err = S.d_err;
-    if (launch_adjoint_tiles(T, &S.tmap, S.dep_ctas, S.dep_threads, S.dep_smem, st) < 0)
+    if (launch_adjoint_tiles(T, &S.tmap, S.dep_ctas, RUBIX_ADJ_THREADS, S.dep_smem, st) < 0)
         return fail(RUBIX_ERR_CUDA, "adjoint launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     launch_adjoint_final(A, P.d_adjpart, S.n_tiles, P.cap, st);
     if (d_global)

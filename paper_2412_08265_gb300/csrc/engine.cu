@@ -440,7 +440,10 @@ std::vector<Buf> plan_buffers(Plan* P, const SspState& S, int n_s, int n_lambda,
         {(void**)&P->d_job_cost, 8 * (size_t)(kMaxJobs + 1)},
     };
     v.insert(v.end(), rest.begin(), rest.end());
-    if (need_tmp || with_grad) v.push_back({(void**)&P->d_tmp, cube});
+    // with gradients d_tmp also holds the loss gradient in pitched rows, so that
+    // the transposed PSF/LSF reads it through a TMA map like the forward
+    if (need_tmp || with_grad)
+        v.push_back({(void**)&P->d_tmp, with_grad ? (size_t)n_s * std::max(pitch0, n_lambda) * sizeof(float) : cube});
     if (with_out) v.push_back({(void**)&P->d_out, cube});
     if (with_grad) {
         v.push_back({(void**)&P->d_contrib, 8 * kGlobal * N});
@@ -542,6 +545,7 @@ rubix_status plan_init(Plan* P, const SspState* S, const rubix_telescope* tel, l
     C.err = S->d_err;
     P->pitch0 = cube0_pitch(C.rp, C.rl, tel->n_lambda);
     P->has_conv_map = false;
+    P->has_grad_map = false;
     P->cap = std::max(n, 1ll);
     P->item_cap = (long long)P->n_s + P->cap / S->chunk + 2;
     P->part_cap = 2 * (P->cap / S->chunk) + 2;
@@ -585,6 +589,17 @@ rubix_status plan_init(Plan* P, const SspState* S, const rubix_telescope* tel, l
             return fail(RUBIX_ERR_CUDA, "cuTensorMapEncodeTiled (PSF/LSF) failed (%d)", (int)r);
         }
         P->has_conv_map = true;
+        if (with_grad && P->d_tmp) {
+            // the same view of d_tmp: the loss gradient, copied into pitched rows by the backward
+            r = enc(&P->grad_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P->d_tmp, gdim, gstr, bx, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                plan_release(P);
+                return fail(RUBIX_ERR_CUDA, "cuTensorMapEncodeTiled (PSF/LSF gradient) failed (%d)", (int)r);
+            }
+            P->has_grad_map = true;
+        }
     }
     return RUBIX_OK;
 }

@@ -113,6 +113,8 @@ struct Plan {
     int pitch0 = 0;                         // row stride of d_cube0 (16-byte rows for the TMA PSF/LSF)
     CUtensorMap conv_map{};                 // 3-D TMA map of d_cube0 for the PSF/LSF kernel
     bool has_conv_map = false;
+    CUtensorMap grad_map{};                 // the same view of d_tmp (backward: pitched loss gradient)
+    bool has_grad_map = false;
     long long* d_job_cost = nullptr;        // deposit launch scratch [kMaxJobs + 1]
     double *d_contrib = nullptr, *d_red = nullptr;
     float2* d_dvda = nullptr;               // backward: dv_los/d(inclination, azimuth) per particle [cap]

@@ -54,7 +54,11 @@ int sm_count();
 #define RUBIX_DEP_GRAB 4
 #endif
 #ifndef RUBIX_ADJ_GRAB
-#define RUBIX_ADJ_GRAB 4
+#define RUBIX_ADJ_GRAB 2
+#endif
+// Threads of an adjoint CTA (one per SM, the deposit's slab geometry).
+#ifndef RUBIX_ADJ_THREADS
+#define RUBIX_ADJ_THREADS 768
 #endif
 
 // K1 parameters. The sort key is spaxel * n_bands + age band (n_bands <= 1:
