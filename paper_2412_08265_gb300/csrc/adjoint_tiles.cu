@@ -17,10 +17,11 @@
 // quad slabs and 31-bin rounds carry over unchanged: lane l reads the quad at
 // node K0 + o_r + l and the neighbour node's quad arrives by shuffle. A warp
 // reduction per (particle, tile) gives part[tile][particle]; K8 adds the
-// tiles in FP64 in tile order.
+// tiles in tile order with a compensated FP32 sum.
 #include "common.cuh"
 #include "kernels.h"
 #include "tile.cuh"
+#include "twosum.cuh"
 
 namespace rubix {
 
@@ -521,33 +522,38 @@ int launch_adjoint_tiles(const AdjTileParams& P, const CUtensorMap* tmap, int n_
 }
 
 // ---------------------------------------------------------------------------
-// K8: tiles summed in FP64 (tile order), chain rule, original order.
+// K8: tiles summed in tile order (compensated FP32), chain rule, original order.
 // ---------------------------------------------------------------------------
 __global__ void k_adj_final(const AdjointParams P, const float4* __restrict__ part, int n_tiles, long long n_cap) {
     const long long n_in = P.seg_off[(long long)P.n_s * P.n_bands];
     const float ln10 = 2.302585092994046f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_in;
          i += (long long)gridDim.x * blockDim.x) {
-        double sm = 0.0, sa = 0.0, sz = 0.0, sv = 0.0;
+        // the tiles' sums in tile order, compensated (two-sum) in FP32
+        float sm = 0.f, sa = 0.f, sz = 0.f, sv = 0.f, em = 0.f, ea = 0.f, ez = 0.f, ev = 0.f;
         for (int t = 0; t < n_tiles; ++t) {
             const float4 v = part[t * n_cap + i];
-            sm += v.x;
-            sa += v.y;
-            sz += v.z;
-            sv += v.w;
+            two_sum_add(sm, em, v.x);
+            two_sum_add(sa, ea, v.y);
+            two_sum_add(sz, ez, v.z);
+            two_sum_add(sv, ev, v.w);
         }
+        sm += em;
+        sa += ea;
+        sz += ez;
+        sv += ev;
         const PartRec pr = P.prec[i];
         int ia, iz;
         float ta, tz, dta, dtz;
         ssp_cell(log10f(pr.age), P.ssp.la_nodes, P.ssp.n_age, ia, ta, dta);
         ssp_cell(log10f(pr.Z), P.ssp.lz_nodes, P.ssp.n_Z, iz, tz, dtz);
         // dt/dv = -(t + ls0/dls) / (c (1 + v/c)): the sums carry the (t + ls0/dls) factor
-        const float q = (float)(-1.0 / (kC_kms * (1.0 + (double)pr.v / kC_kms)));
+        const float q = -1.f / ((float)kC_kms + pr.v);  // = -1 / (c (1 + v/c))
         const float fs = (float)P.flux_scale;
-        const float dm = fs * (float)sm;
-        const float dage = fs * pr.mass * dta * (float)sa / (pr.age * ln10);
-        const float dZ = fs * pr.mass * dtz * (float)sz / (pr.Z * ln10);
-        const float dv = fs * pr.mass * q * (float)sv;
+        const float dm = fs * sm;
+        const float dage = fs * pr.mass * dta * sa / (pr.age * ln10);
+        const float dZ = fs * pr.mass * dtz * sz / (pr.Z * ln10);
+        const float dv = fs * pr.mass * q * sv;
         const int p = P.perm[i];
         if (P.d_mass) P.d_mass[p] = dm;
         if (P.d_age) P.d_age[p] = dage;

@@ -3,6 +3,7 @@
 // spaxels, summed from their work items' partial rows.
 #include "common.cuh"
 #include "kernels.h"
+#include "twosum.cuh"
 
 namespace rubix {
 
@@ -50,12 +51,6 @@ int launch_zero_empty(const int* seg_off, int n_s, int nb, float* cube, int pitc
 // one FP32 rounding, as with an FP64 accumulator, without the FP64 pipe,
 // which on this GPU runs at 1/64 of the FP32 rate.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum_add(float& s, float& c, float x) {
-    const float t = s + x;
-    const float z = t - s;
-    c += (s - (t - z)) + (x - z);
-    s = t;
-}
 
 // The split spaxels, compacted (in any order: each row's sum is in item order,
 // so the result does not depend on it); list[n_s] counts them.
