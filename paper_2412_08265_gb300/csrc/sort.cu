@@ -305,13 +305,20 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const int* __res
 }
 
 // seg_off[s] = first sorted position with key >= s, for s in [0, n_keys]; the
-// sorted keys are in [0, n_keys).
+// sorted keys are in [0, n_keys). One thread per segment boundary, each a
+// binary search over the sorted keys, so that the work per thread is bounded
+// however the particles are spread (a small galaxy in a large field leaves
+// runs of hundreds of thousands of empty segments, which one thread per
+// particle would write one after another).
 __global__ void k_seg_bounds(const int* __restrict__ skeys, long long n, int n_keys, int* __restrict__ seg_off) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= n;
-         i += (long long)gridDim.x * blockDim.x) {
-        int prev = (i == 0) ? -1 : skeys[i - 1];
-        int cur = (i == n) ? n_keys : skeys[i];
-        for (int s = prev + 1; s <= cur; ++s) seg_off[s] = (int)i;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s <= n_keys;
+         s += (long long)gridDim.x * blockDim.x) {
+        long long lo = 0, hi = n;
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if (skeys[mid] < s) lo = mid + 1; else hi = mid;
+        }
+        seg_off[s] = (int)lo;
     }
 }
 
@@ -352,9 +359,9 @@ int launch_sort_by_key(const int* keys, long long n, int n_keys, int* keys_tmp, 
             vin = vout;
         }
     }
-    int nt = (int)((n + 1 + 255) / 256);
-    if (nt > 4096) nt = 4096;
-    k_seg_bounds<<<nt, 256, 0, st>>>(keys_out, n, n_keys, seg_off);
+    long long nt = ((long long)n_keys + 1 + 255) / 256;
+    if (nt > 16ll * sm_count()) nt = 16ll * sm_count();
+    k_seg_bounds<<<(int)nt, 256, 0, st>>>(keys_out, n, n_keys, seg_off);
     return launches + 1;
 }
 
