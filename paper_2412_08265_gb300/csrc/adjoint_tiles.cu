@@ -15,7 +15,7 @@
 // corner's slope times the bin position) and apply w, a and b once per
 // particle and tile. The deposit's (tile, work item, age band) partition,
 // quad slabs and 31-bin rounds carry over unchanged: lane l reads the quad at
-// node K0 + o_r + l and the neighbour node's quad arrives by shuffle. A warp
+// node K0 + o_r + l and the neighbouring node's quad from the slab. A warp
 // reduction per (particle, tile) gives part[tile][particle]; K8 adds the
 // tiles in tile order with a compensated FP32 sum.
 #include "common.cuh"
@@ -114,9 +114,11 @@ __device__ __noinline__ AdjSums adj_general(const float4 w, const float4 g4, con
 // 2, 3): U_c = sum_j G_j V_c(j), V_c(j) the corner template interpolated at
 // bin j, and T_c = sum_j G_j u_j (T_c[hi] - T_c[lo]), the slope between the
 // bracketing nodes times the bin's absolute position u_j = t_j + ls0/dls.
-// Lane l reads node K0 + o_r + l's quad and takes the neighbouring node's
-// from lane l -+ 1 (four shuffles). Afterwards sm = w.U, sa = a.U, sz = b.U
-// and sv = w.T.
+// Lane l reads node K0 + o_r + l's quad and the neighbouring node's (node
+// K0 + o_r + l -+ 1, one more 16-byte load: as the four shuffles of lane
+// l -+ 1's quad it replaces, four shared-memory wavefronts, conflict-free, as
+// the lanes of each quarter-warp read at most eight consecutive nodes).
+// Afterwards sm = w.U, sa = a.U, sz = b.U and sv = w.T.
 template <int R>
 __device__ __forceinline__ AdjSums adj_particle(const float4 w, const float4 g4, const TileCtx& C,
                                                 const float4* __restrict__ slab, const float4* __restrict__ quad,
@@ -145,10 +147,12 @@ __device__ __forceinline__ AdjSums adj_particle(const float4 w, const float4 g4,
     for (int r = 0; r < R; ++r) {
         const float4 Q = *q;
         const float g = f + nld;
-        const bool neg = g < 0.f;
-        const int src = neg ? lane - 1 : lane + 1;
-        const float2 X01 = make_float2(__shfl_sync(0xffffffffu, Q.x, src), __shfl_sync(0xffffffffu, Q.y, src));
-        const float2 X23 = make_float2(__shfl_sync(0xffffffffu, Q.z, src), __shfl_sync(0xffffffffu, Q.w, src));
+        // lane 31 owns no bin (G = 0); it takes node - 1, so that every read
+        // stays within nodes K0 .. K0 + 31 R of the slab
+        const bool neg = g < 0.f || lane == 31;
+        const float4 Xq = q[neg ? -C.ncb : C.ncb];
+        const float2 X01 = make_float2(Xq.x, Xq.y);
+        const float2 X23 = make_float2(Xq.z, Xq.w);
         const float2 Q01 = make_float2(Q.x, Q.y), Q23 = make_float2(Q.z, Q.w);
         const float2 D01 = __fadd2_rn(X01, make_float2(-Q.x, -Q.y));
         const float2 D23 = __fadd2_rn(X23, make_float2(-Q.z, -Q.w));
