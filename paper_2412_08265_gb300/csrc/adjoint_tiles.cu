@@ -450,10 +450,16 @@ __global__ void __launch_bounds__(RUBIX_ADJ_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
                             qe = min(qe, P.seg_off[(long long)sp * nb + band + 1]);
                         }
                         live = qb < qe;
-                        // the item's first weights and record, on their way to L1
+                        // the item's first weights and record, on their way to L1,
+                        // and its tile slice of dL/dcube0 on its way to L2
                         if (live) {
                             asm volatile("prefetch.global.L1 [%0];" ::"l"(P.wu + qb));
                             asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * qb + 1));
+                            const float* gs = P.G0 + (long long)sp * P.n_lambda + C.j0;
+                            const int nbin = min(P.tile_w + 1, P.n_lambda - C.j0);
+#pragma unroll 1
+                            for (int o = 0; o < nbin; o += 32)
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(gs + o));
                         }
                     }
                 }
