@@ -97,9 +97,10 @@ __global__ void __launch_bounds__(256) k_psfy_noise(const ConvParams P, const fl
 // Fused single pass for the common radii (compile-time rp, rl): one CTA owns an
 // (x block of kFX spaxels, wavelength chunk of kFL = 32 bins, y band of kFY
 // rows) and streams the input rows of its band, plus rp halo rows, through a
-// cp.async pipeline (zero fill outside the cube). For each input row: LSF along
-// wavelength into shared memory (lanes run along wavelength, warps over x),
-// then PSF along x; the PSF-x value of input row y_in is added, with weight
+// cp.async pipeline (zero fill outside the cube). For each input row: PSF along
+// x into shared memory (each warp its own output columns, over the tile's
+// bins and the LSF halo; lanes run along wavelength), then LSF along
+// wavelength; the value of input row y_in is added, with weight
 // gp[m], to the register accumulator of output row y_in - rp + m (the 2 rp + 1
 // accumulators of each owned (x, wavelength) rotate with the row, the loop
 // being unrolled by 2 rp + 1 so their indices are static). After row y_in the
@@ -123,7 +124,7 @@ constexpr int kFStages = RUBIX_PSF_STAGES;
 
 template <int RP, int RL>
 constexpr size_t fused_smem_bytes() {
-    return sizeof(float) * ((size_t)kFStages * (kFX + 2 * RP) * (kFL + 2 * RL) + (size_t)(kFX + 2 * RP) * kFL);
+    return sizeof(float) * ((size_t)kFStages * (kFX + 2 * RP) * (kFL + 2 * RL) + (size_t)kFX * (kFL + 2 * RL));
 }
 
 __device__ __forceinline__ float add_noise(float v, long long idx, const ConvParams& P) {
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kFThreads) k_psf_lsf_fused(const ConvParams P,
     constexpr int XW = kFX + 2 * RP, LW = kFL + 2 * RL, NR = 2 * RP + 1;
     extern __shared__ float sm[];
     float* s_in = sm;                        // [kFStages][XW][LW]
-    float* s_l = s_in + kFStages * XW * LW;  // [XW][kFL]   LSF output
+    float* s_x = s_in + kFStages * XW * LW;  // [kFX][LW]   PSF-x output (row xo written and read by its warp)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j0 = blockIdx.x * kFL;
     const int x0 = blockIdx.y * kFX;
@@ -200,25 +201,29 @@ __global__ void __launch_bounds__(kFThreads) k_psf_lsf_fused(const ConvParams P,
                 if (ahead < n_rows) load_row(ahead, abuf);  // that buffer was read in iteration i - 1
                 else cp_async_commit();
                 cp_async_wait<kFStages - 1>();
-                __syncthreads();  // row i landed; every warp is done with s_l of row i - 1
+                __syncthreads();  // row i landed
                 const float* src = s_in + buf * XW * LW;
                 if (++buf == kFStages) buf = 0;
-                for (int xi = warp; xi < XW; xi += kFWarps) {
-                    const float* r = src + xi * LW + lane;
-                    float a = 0.f;
 #pragma unroll
-                    for (int d = 0; d <= 2 * RL; ++d) a = fmaf(gl[d], r[d], a);
-                    s_l[xi * kFL + lane] = a;
+                for (int k = 0; k < kFXW; ++k) {
+                    const int xo = warp + k * kFWarps;
+                    for (int l = lane; l < LW; l += 32) {
+                        const float* c = src + xo * LW + l;
+                        float a = 0.f;
+#pragma unroll
+                        for (int d = 0; d < NR; ++d) a = fmaf(gp[d], c[d * LW], a);
+                        s_x[xo * LW + l] = a;
+                    }
                 }
-                __syncthreads();
+                __syncthreads();  // every warp is done with row i's input buffer
                 const int y_done = y0 + i - 2 * RP;  // output row completed by this input row
 #pragma unroll
                 for (int k = 0; k < kFXW; ++k) {
                     const int xi = warp + k * kFWarps;
-                    const float* c = s_l + xi * kFL + lane;
+                    const float* r = s_x + xi * LW + lane;
                     float v = 0.f;
 #pragma unroll
-                    for (int d = 0; d < NR; ++d) v = fmaf(gp[d], c[d * kFL], v);
+                    for (int d = 0; d <= 2 * RL; ++d) v = fmaf(gl[d], r[d], v);
 #pragma unroll
                     for (int m = 0; m < NR; ++m) acc[k][(ph + m) % NR] = fmaf(gp[m], v, acc[k][(ph + m) % NR]);
                     // accumulator (ph + 0) % NR holds output row y_in - RP = y_done: complete
@@ -263,16 +268,22 @@ static bool try_fused(const ConvParams& P, const float* in, float* out, cudaStre
 
 // ----------------------------------------------------------------------------
 // TMA variant of the fused pass for a cube whose rows are 16-byte aligned (the
-// deposit's own pitched cube). One CTA owns kTL = 128 bins x kTX = 8 spaxels
-// along x (one per warp) x kTY rows along y; four CTAs per SM (63 registers:
-// 8 spaxels with four CTAs ran 0.78 ms on the 300x300x3721 cube, 16 spaxels
-// with two CTAs 0.85 ms). Each input row arrives as one 3-D TMA box
-// (bins j0 - RLa .. j0 + kTL + RLa, spaxels x0 - rp .. x0 + kTX + rp; zero fill
-// outside the cube is the zero padding) in a kTS-stage mbarrier ring. A lane
-// computes 4 consecutive bins: the LSF from 16-byte shared loads into a
-// double-buffered row, then the PSF along x and the rotating PSF-y
-// accumulators of the previous kernel, in the same summation order, so the
-// result is bitwise that of the cp.async kernel. One barrier per input row.
+// deposit's own pitched cube). One CTA owns kTX = 8 spaxels along x (one per
+// warp) x kTY rows along y x kTL = kTB - 2 RLa bins. Each input row arrives
+// as one 3-D TMA box (kTB = 128 bins from j0 - RLa, spaxels x0 - rp ..
+// x0 + kTX + rp; zero fill outside the cube is the zero padding) in a
+// kTS-stage mbarrier ring. Warp w owns output column x0 + w and lane q the
+// box's bins 4q .. 4q + 3:
+//   PSF along x: the lane's 4 bins of column w from the box's columns
+//     w .. w + 2 rp, into the warp's own row of px (so every bin the LSF
+//     needs, halo included, is computed once, by the warp that reads it);
+//   LSF along wavelength from the warp's px row (lanes RLa/4 .. 31 - RLa/4,
+//     whose bins are the tile's), then the rotating PSF-y register
+//     accumulators.
+// One CTA barrier per input row (every warp is done with the stage before it
+// is refilled); px is private to its warp. The terms of each output are
+// summed in the order of the cp.async kernel (PSF x, LSF, PSF y; each over
+// its taps in order), so the cube is bitwise the same.
 // ----------------------------------------------------------------------------
 #ifndef RUBIX_PSF_TY
 #define RUBIX_PSF_TY 150
@@ -283,17 +294,19 @@ static bool try_fused(const ConvParams& P, const float* in, float* out, cudaStre
 #ifndef RUBIX_PSF_TMINB
 #define RUBIX_PSF_TMINB 4       // CTAs per SM the register budget is sized for
 #endif
-constexpr int kTL = 128, kTX = 8, kTThreads = 256, kTWarps = kTThreads / 32, kTXW = kTX / kTWarps;
+constexpr int kTB = 128, kTX = 8, kTThreads = 256, kTWarps = kTThreads / 32;
 constexpr int kTY = RUBIX_PSF_TY, kTS = RUBIX_PSF_TSTAGES;
+static_assert(kTX == kTWarps, "one output column per warp");
 
 template <int RP, int RL>
 struct TmaGeo {
     static constexpr int RLa = (RL + 3) / 4 * 4;  // wavelength halo rounded up to 16 bytes
-    static constexpr int LW = kTL + 2 * RLa;      // box: bins
+    static constexpr int LW = kTB;                // box: bins
+    static constexpr int TL = kTB - 2 * RLa;      // output bins per tile
     static constexpr int XW = kTX + 2 * RP;       // box: spaxels along x
     static constexpr int NV = 1 + RLa / 2;        // 16-byte loads per lane for 4 LSF outputs
-    static constexpr int stage_floats = (LW * XW + 31) / 32 * 32;  // 128-byte aligned stages
-    static constexpr size_t smem = 128 + (size_t)kTS * stage_floats * 4 + 2 * (size_t)XW * kTL * 4;
+    static constexpr int stage_floats = LW * XW;  // 512-byte rows: stages stay 128-byte aligned
+    static constexpr size_t smem = 128 + (size_t)kTS * stage_floats * 4 + (size_t)kTX * kTB * 4;
 };
 
 template <int RP, int RL>
@@ -302,12 +315,13 @@ __global__ void __launch_bounds__(kTThreads, RUBIX_PSF_TMINB) k_psf_lsf_tma(cons
                                                            float* __restrict__ out) {
     using G = TmaGeo<RP, RL>;
     constexpr int NR = 2 * RP + 1;
+    constexpr int Q0 = G::RLa / 4, Q1 = 32 - G::RLa / 4;  // lanes whose bins are the tile's
     extern __shared__ __align__(1024) float smt[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smt);
     float* stages = smt + 32;  // 128 bytes in
-    float* s_l = stages + kTS * G::stage_floats;  // [2][XW][kTL] LSF output
+    float* px = stages + kTS * G::stage_floats;  // [kTX][kTB] PSF-x output, one row per warp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j0 = blockIdx.x * kTL, x0 = blockIdx.y * kTX, y0 = blockIdx.z * kTY;
+    const int j0 = blockIdx.x * G::TL, x0 = blockIdx.y * kTX, y0 = blockIdx.z * kTY;
     const int y1 = min(y0 + kTY, P.ny);
     const int nx = P.nx, nl = P.n_lambda;
     const int n_rows = (y1 - y0) + 2 * RP;  // input rows y0 - RP .. y1 + RP - 1
@@ -330,13 +344,15 @@ __global__ void __launch_bounds__(kTThreads, RUBIX_PSF_TMINB) k_psf_lsf_tma(cons
     if (threadIdx.x == 0)
         for (int i = 0; i < min(kTS, n_rows); ++i) issue(i);
 
-    float acc[kTXW][NR][4];
+    float acc[NR][4];
 #pragma unroll
-    for (int k = 0; k < kTXW; ++k)
+    for (int m = 0; m < NR; ++m)
 #pragma unroll
-        for (int m = 0; m < NR; ++m)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[k][m][u] = 0.f;
+        for (int u = 0; u < 4; ++u) acc[m][u] = 0.f;
+    float* prow = px + warp * kTB;
+    const bool owns = lane >= Q0 && lane < Q1;
+    const int x = x0 + warp;
+    const int jl = j0 - G::RLa + 4 * lane;  // cube bin of the lane's first box bin
 
     for (int ib = 0; ib < n_rows; ib += NR) {
 #pragma unroll
@@ -345,30 +361,19 @@ __global__ void __launch_bounds__(kTThreads, RUBIX_PSF_TMINB) k_psf_lsf_tma(cons
             if (i < n_rows) {
                 const int s = i % kTS;
                 const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((i / kTS) & 1), 2000000000ll);
-                const float* src = stages + s * G::stage_floats;
-                float* dl = s_l + (i & 1) * G::XW * kTL;
                 if (ok) {
-                    for (int xi = warp; xi < G::XW; xi += kTWarps) {
-                        const float4* r4 = reinterpret_cast<const float4*>(src + xi * G::LW + 4 * lane);
-                        float v[4 * G::NV];
+                    // PSF along x: box columns warp .. warp + 2 RP, bins 4 lane .. 4 lane + 3
+                    const float* src = stages + s * G::stage_floats + warp * G::LW + 4 * lane;
+                    float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                        for (int c = 0; c < G::NV; ++c) {
-                            const float4 t = r4[c];
-                            v[4 * c] = t.x;
-                            v[4 * c + 1] = t.y;
-                            v[4 * c + 2] = t.z;
-                            v[4 * c + 3] = t.w;
-                        }
-                        float o[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            float a = 0.f;
-#pragma unroll
-                            for (int d = 0; d <= 2 * RL; ++d) a = fmaf(gl[d], v[u + d + G::RLa - RL], a);
-                            o[u] = a;
-                        }
-                        *reinterpret_cast<float4*>(dl + xi * kTL + 4 * lane) = make_float4(o[0], o[1], o[2], o[3]);
+                    for (int d = 0; d < NR; ++d) {
+                        const float4 c = *reinterpret_cast<const float4*>(src + d * G::LW);
+                        a[0] = fmaf(gp[d], c.x, a[0]);
+                        a[1] = fmaf(gp[d], c.y, a[1]);
+                        a[2] = fmaf(gp[d], c.z, a[2]);
+                        a[3] = fmaf(gp[d], c.w, a[3]);
                     }
+                    *reinterpret_cast<float4*>(prow + 4 * lane) = make_float4(a[0], a[1], a[2], a[3]);
                 }
                 if (__syncthreads_or(!ok)) {
                     // a load did not complete in time: record it, let the copies in
@@ -380,32 +385,39 @@ __global__ void __launch_bounds__(kTThreads, RUBIX_PSF_TMINB) k_psf_lsf_tma(cons
                     }
                     return;
                 }
-                // every warp is done with stage s: refill it
+                // every warp is done with stage s (and the barrier made this
+                // warp's px row visible to its lanes): refill it
                 if (threadIdx.x == 0 && i + kTS < n_rows) issue(i + kTS);
                 const int y_done = y0 + i - 2 * RP;  // output row completed by this input row
+                if (owns) {
+                    // LSF along wavelength from px: bins 4 lane - RLa .. 4 lane + 3 + RLa
+                    const float4* r4 = reinterpret_cast<const float4*>(prow + 4 * lane - G::RLa);
+                    float v[4 * G::NV];
 #pragma unroll
-                for (int k = 0; k < kTXW; ++k) {
-                    const int xo = warp * kTXW + k;
-                    float vv[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int c = 0; c < G::NV; ++c) {
+                        const float4 t = r4[c];
+                        v[4 * c] = t.x;
+                        v[4 * c + 1] = t.y;
+                        v[4 * c + 2] = t.z;
+                        v[4 * c + 3] = t.w;
+                    }
+                    float o[4];
 #pragma unroll
-                    for (int d = 0; d < NR; ++d) {
-                        const float4 c = *reinterpret_cast<const float4*>(dl + (xo + d) * kTL + 4 * lane);
-                        vv[0] = fmaf(gp[d], c.x, vv[0]);
-                        vv[1] = fmaf(gp[d], c.y, vv[1]);
-                        vv[2] = fmaf(gp[d], c.z, vv[2]);
-                        vv[3] = fmaf(gp[d], c.w, vv[3]);
+                    for (int u = 0; u < 4; ++u) {
+                        float b = 0.f;
+#pragma unroll
+                        for (int d = 0; d <= 2 * RL; ++d) b = fmaf(gl[d], v[u + d + G::RLa - RL], b);
+                        o[u] = b;
                     }
 #pragma unroll
                     for (int m = 0; m < NR; ++m)
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            acc[k][(ph + m) % NR][u] = fmaf(gp[m], vv[u], acc[k][(ph + m) % NR][u]);
-                    float* done = acc[k][ph % NR];
-                    const int x = x0 + xo;
+                        for (int u = 0; u < 4; ++u) acc[(ph + m) % NR][u] = fmaf(gp[m], o[u], acc[(ph + m) % NR][u]);
+                    float* done = acc[ph % NR];
                     if (y_done >= y0 && x < nx) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
-                            const int j = j0 + 4 * lane + u;
+                            const int j = jl + u;
                             if (j < nl) {
                                 const long long idx = ((long long)y_done * nx + x) * nl + j;
                                 out[idx] = (P.noise_inv_s2n > 0.f) ? add_noise(done[u], idx, P) : done[u];
@@ -415,6 +427,7 @@ __global__ void __launch_bounds__(kTThreads, RUBIX_PSF_TMINB) k_psf_lsf_tma(cons
 #pragma unroll
                     for (int u = 0; u < 4; ++u) done[u] = 0.f;
                 }
+                __syncwarp();  // the warp's px row is rewritten by the next input row
             }
         }
     }
@@ -442,7 +455,8 @@ static bool launch_tma(const ConvParams& P, const CUtensorMap* map, float* out, 
     if (cudaFuncSetAttribute(k_psf_lsf_tma<RP, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return false;
-    dim3 g((P.n_lambda + kTL - 1) / kTL, (P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY);
+    constexpr int TL = TmaGeo<RP, RL>::TL;
+    dim3 g((P.n_lambda + TL - 1) / TL, (P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY);
     k_psf_lsf_tma<RP, RL><<<g, kTThreads, smem, st>>>(P, *map, out);
     return true;
 }
