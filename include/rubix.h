@@ -22,7 +22,11 @@
  *       R20 = si sa                R21 = si ca                   R22 = ci
  *     x' = (R00 x + R01 y) + R02 z, y' likewise, v_los = (R20 vx + R21 vy) + R22 vz,
  *     no FMA. With a = q = 0: x' = x, y' = y cos i - z sin i,
- *     v_los = vy sin i + vz cos i.
+ *     v_los = vy sin i + vz cos i. (The library decides each key from an FP32
+ *     evaluation with an error bound and falls back to this FP64 expression
+ *     near spaxel edges, so keys are those of the FP64 expression; v_los,
+ *     which decides no integer, is evaluated in FP32 with FMA, within a few
+ *     FP32 ulps of the expression.)
  *   - Spaxels: nx*ny squares of side spaxel_size centred on (0, 0), half-open;
  *     x_lo = (-0.5*nx)*size, u = (x' - x_lo) * (1/size) in FP64, ix = floor(u).
  *     Particles outside the field are dropped.
