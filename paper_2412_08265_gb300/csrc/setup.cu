@@ -10,17 +10,70 @@
 namespace rubix {
 
 // ----------------------------------------------------------------------------
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi) / 2), about 48 significant bits. Products use the
+// exact FMA residual, sums Knuth's two-sum; each operation is a handful of
+// FP32 instructions instead of one FP64 instruction on this GPU's FP64 pipe,
+// which runs at 1/64 of the FP32 rate (Dekker 1971; Shewchuk 1997).
+// ----------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+// (the _rn intrinsics keep the compiler from contracting these products and
+// sums into FMAs, which the error-free transformations must not see)
+__device__ __forceinline__ DF df_norm(float hi, float lo) {  // |hi| >= |lo|
+    const float s = __fadd_rn(hi, lo);
+    return DF{s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+
+__device__ __forceinline__ DF df_of(double x) {
+    const float hi = (float)x;
+    return DF{hi, (float)(x - (double)hi)};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float z = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
+    return df_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.hi, -p);
+    return df_norm(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    const float e = fmaf(a.hi, b, -p);
+    return df_norm(p, fmaf(a.lo, b, e));
+}
+
+// ----------------------------------------------------------------------------
 // K3: per-particle setup (sorted order).
 // ----------------------------------------------------------------------------
 __global__ void k_setup(SetupParams P) {
     const long long n_in = P.seg_off[(long long)P.n_s * P.n_bands];
     if (n_in > P.n_cap) return;
     const int n_ls = P.ssp.n_ls;
+    // t(j) = ((l0 + j dl) / dop - ls0) / dls = B + j A with dop = (1 + z)(1 + v/c).
+    // With alpha_z = 1 / ((1 + z) dls) and g = (v/c) / (1 + v/c), so that
+    // 1 / (1 + v/c) = 1 - g:
+    //   A = A_z (1 - g),   A_z = dl alpha_z,
+    //   B = B_z - L g,     L = l0 alpha_z,  B_z = L - ls0/dls,
+    // (bin means: B - A/2, the bin's lower edge), the particle's part in
+    // double-float from the FP64 constants below (converted once per thread).
+    const DF Az = df_of(P.dl * P.alpha_z), L = df_of(P.l0 * P.alpha_z);
+    const DF Bz = df_of(fma(P.l0, P.alpha_z, -P.ls0_dls)), invc = df_of(P.inv_c);
+    const float t_lastj = (float)(P.resample ? P.n_lambda : P.n_lambda - 1);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_in;
          i += (long long)gridDim.x * blockDim.x) {
         const PartRec pr = P.pin[P.perm[i]];
         const float m = pr.mass, age = pr.age, Z = pr.Z;
-        const double v = (double)pr.v;
         int ia, iz;
         float ta, tz, dta, dtz;
         ssp_cell(log10f(age), P.ssp.la_nodes, P.ssp.n_age, ia, ta, dta);
@@ -32,36 +85,34 @@ __global__ void k_setup(SetupParams P) {
         r.w[2] = ms * ((1.f - ta) * tz);
         r.w[3] = ms * (ta * tz);
         const int c0 = ia * max(P.ssp.n_Z - 1, 1) + iz;  // SSP cell of the four corners
-        // t(j) = ((l0 + j dl) / dop - ls0) / dls = B + j A   (FP64), with
-        // dop = (1 + z)(1 + v/c): alpha = 1 / (dop dls) = alpha_z / (1 + v/c),
-        // alpha_z = 1 / ((1 + z) dls) and ls0 / dls from the host. The one
-        // reciprocal per particle is the FP32 reciprocal refined by one
-        // Newton-Raphson step in FP64, r0 (2 - q r0): the error squares,
-        // from 2^-24 to about 2^-48 relative -- 1e-11 node units over 3721
-        // nodes, far below the FP32 deposit's resolution -- on GB300's FP64
-        // pipe (1/64 of the FP32 rate) at a fraction of a correctly rounded
-        // division's cost.
-        const double q = 1.0 + v * P.inv_c;
-        const double r0 = (double)__frcp_rn((float)q);
-        const double rq = r0 * fma(-q, r0, 2.0);
-        const double alpha = P.alpha_z * rq;
-        // bin means: the record maps j to bin j's lower edge, t(j) - A/2,
-        // and the edges run j = 0 .. n_lambda
-        const double A = P.dl * alpha;
-        const double B = fma(P.l0, alpha, -P.ls0_dls) - (P.resample ? 0.5 * A : 0.0);
-        const double t_last = fma(A, (double)(P.resample ? P.n_lambda : P.n_lambda - 1), B);
+        // b = v/c, q = 1 + b, g = b / q: one FP32 quotient and one correction
+        // from the double-float residual b - g0 q (relative error ~2^-46)
+        const DF b = df_mul_f(invc, pr.v);
+        const DF q = df_add(DF{1.f, 0.f}, b);
+        const float g0 = __fdiv_rn(b.hi, q.hi);
+        const DF res = df_add(b, df_neg(df_mul_f(q, g0)));
+        const DF g = df_norm(g0, __fdiv_rn(res.hi, q.hi));
+        const DF A = df_add(Az, df_neg(df_mul(Az, g)));
+        DF B = df_add(Bz, df_neg(df_mul(L, g)));
+        if (P.resample) B = df_add(B, DF{-0.5f * A.hi, -0.5f * A.lo});
+        const float t_last = fmaf(A.hi, t_lastj, B.hi);
         int bi = 0;
         float bf = 0.f, a_hi = 0.f, a_lo = 0.f;
-        if (!(q > 0.0) || !(B < (double)n_ls) || !(t_last >= -1.0) || !(B > -32768.0)) {
+        if (!(q.hi > 0.f) || !(B.hi < (float)n_ls) || !(t_last >= -1.f) || !(B.hi > -32768.f)) {
             // the spectrum misses every output bin (a_hi = 0 marks the record)
             r.w[0] = r.w[1] = r.w[2] = r.w[3] = 0.f;
         } else {
-            const double fb = floor(B);
+            // B = bi + bf, bf in [0, 1] rounded once; A = a_hi + a_lo with
+            // a_hi of 11 significant bits, so that j a_hi is exact in FP32
+            const float fb = floorf(B.hi);
             bi = (int)fb;
-            bf = (float)(B - fb);
-            const double ah = __longlong_as_double(__double_as_longlong(A) & ~((1ll << 42) - 1));
-            a_hi = (float)ah;
-            a_lo = (float)(A - ah);
+            bf = __fadd_rn(__fsub_rn(B.hi, fb), B.lo);
+            if (bf < 0.f) {
+                bf += 1.f;
+                --bi;
+            }
+            a_hi = __uint_as_float(__float_as_uint(A.hi) & ~((1u << 13) - 1u));
+            a_lo = __fadd_rn(__fsub_rn(A.hi, a_hi), A.lo);
         }
         r.c0_bi = (c0 << 16) | (bi & 0xffff);
         r.bf = bf;
