@@ -90,7 +90,11 @@ __device__ __noinline__ AdjSums adj_general(const float4 w, const float4 g4, con
         const int k = node_pos(j, bi, g4.y, g4.z, g4.w, f);
         float4 q0, q1;
         if (use_slab) {
-            const float4* p = slab + (k - C.klo) * C.ncb + (cell - C.cell0);
+            const int e = (k - C.klo) * C.ncb + (cell - C.cell0);
+#if RUBIX_DEBUG
+            dbg_check(e >= 0 && e + C.ncb < C.slab_w * C.ncb, C.err);
+#endif
+            const float4* p = slab + e;
             q0 = p[0];
             q1 = p[C.ncb];
         } else {
@@ -134,6 +138,11 @@ __device__ __forceinline__ AdjSums adj_particle(const float4 w, const float4 g4,
     if (!(delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R) &&
           (unsigned)cr < (unsigned)C.ncb))
         return adj_general<R>(w, g4, C, slab, quad, lane, grow, ls0_over);
+#if RUBIX_DEBUG
+    // each lane's node and the neighbour it reads (lane 0: node + 1, lane 31: node - 1)
+    dbg_check(dbg_rounds_in_slab(kw * C.ncb + cr, f, delta, C, lane, R, 31, 31, lane > 0 ? -1 : 0, lane < 31 ? 1 : 0),
+              C.err);
+#endif
     const float4* q = slab + (kw + lane) * C.ncb + cr;
     const int s31 = 31 * C.ncb, s30 = 30 * C.ncb;
     const float nld = -lanef * delta;
@@ -201,6 +210,10 @@ __device__ __noinline__ AdjSums adj_mean_bin(const float4 w, const float4 wa, co
     const int ka = node_pos(j, bi, g4.y, g4.z, g4.w, fa);
     const int kb = node_pos(j + 1, bi, g4.y, g4.z, g4.w, fb);
     auto node = [&](int k) {
+#if RUBIX_DEBUG
+        if (use_slab)
+            dbg_check((unsigned)((k - C.klo) * C.ncb + (cell - C.cell0)) < (unsigned)(C.slab_w * C.ncb), C.err);
+#endif
         return use_slab ? slab[(k - C.klo) * C.ncb + (cell - C.cell0)] : quad_global(quad, C, cell, k);
     };
     const float len = (float)(kb - ka) + (fb - fa);
@@ -292,6 +305,9 @@ __device__ __forceinline__ AdjSums adj_mean_particle(const float4 w, const float
     if (!(delta >= 0.f && delta * 31.f < 1.f && (unsigned)kw < (unsigned)(C.slab_w - 31 * R - 1) &&
           (unsigned)cr < (unsigned)C.ncb))
         return adj_mean_general<R>(w, g4, C, slab, quad, lane, grow, ls0_over);
+#if RUBIX_DEBUG
+    dbg_check(dbg_rounds_in_slab(kw * C.ncb + cr, f, delta, C, lane, R + 1, 30, R + 1, 0, 0), C.err);
+#endif
     const float4* q = slab + (kw + lane) * C.ncb + cr;
     const int s30 = 30 * C.ncb, s29 = 29 * C.ncb;
     const float nld = -lanef * delta;
@@ -391,6 +407,9 @@ __global__ void __launch_bounds__(RUBIX_ADJ_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
     C.n_cells = P.n_cells;
     C.q16 = P.quad16;
     C.qdt = P.qdt;
+#if RUBIX_DEBUG
+    C.err = P.err;
+#endif
     const uint32_t slab_bytes = (uint32_t)P.n_boxes * (uint32_t)P.box_w * (uint32_t)P.ncb * sizeof(float4);
     uint32_t phase = 0;
     const float4* __restrict__ rec4 = reinterpret_cast<const float4*>(P.rec);
@@ -502,6 +521,9 @@ __global__ void __launch_bounds__(RUBIX_ADJ_THREADS, RUBIX_DEP_CTAS) k_adjoint_t
                         float c = (hi8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, hi8 ? b0 : b1, 8);
 #pragma unroll
                         for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+#if RUBIX_DEBUG
+                        dbg_check(q >= 0 && q < P.n_cap, P.err);
+#endif
                         if ((lane & 7) == 0) reinterpret_cast<float*>(part + q)[lane >> 3] = c;
                     }
                 }

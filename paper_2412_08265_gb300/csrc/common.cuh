@@ -15,7 +15,24 @@ constexpr double kC_kms = 299792.458;
 enum DeviceError : unsigned {
     kErrTmaTimeout = 1u,      // a bounded mbarrier wait on a TMA slab load expired
     kErrBadItem = 2u,         // a work item pointed outside its buffers
+    kErrBounds = 4u,          // debug builds: a computed index fell outside its buffer
 };
+
+// Debug builds (RUBIX_DEBUG=1, a separate library built by the tests) check
+// the shared-memory and record indices the deposit and the adjoint compute
+// against their buffers and set kErrBounds instead of faulting; release
+// builds compile none of it.
+#ifndef RUBIX_DEBUG
+#define RUBIX_DEBUG 0
+#endif
+__device__ __forceinline__ void dbg_check(bool ok, unsigned* err) {
+#if RUBIX_DEBUG
+    if (!ok && err) atomicOr(err, kErrBounds);
+#else
+    (void)ok;
+    (void)err;
+#endif
+}
 
 // ----------------------------------------------------------------------------
 // Shared-memory barrier and TMA (inline PTX, sm_90+ forms valid on sm_103a)

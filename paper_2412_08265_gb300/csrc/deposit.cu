@@ -78,7 +78,11 @@ __device__ __noinline__ float bin_value(const float4 w4, const float4 g4, const 
     const int k = node_pos(j, rec_bi(c0_bi), g4.y, g4.z, g4.w, f);
     float4 q0, q1;
     if (use_slab) {
-        const float4* p = slab + (k - C.klo) * C.ncb + (cell - C.cell0);
+        const int e = (k - C.klo) * C.ncb + (cell - C.cell0);
+#if RUBIX_DEBUG
+        dbg_check(e >= 0 && e + C.ncb < C.slab_w * C.ncb, C.err);
+#endif
+        const float4* p = slab + e;
         q0 = p[0];
         q1 = p[C.ncb];
     } else {
@@ -177,9 +181,12 @@ __device__ __forceinline__ void deposit_particle(const float4 w4, const float4 g
                                                  unsigned long long* slow_count) {
     int base;
     float f, delta;
-    if (fast_setup<R>(g4, C, base, f, delta))
+    if (fast_setup<R>(g4, C, base, f, delta)) {
+#if RUBIX_DEBUG
+        dbg_check(dbg_rounds_in_slab(base, f, delta, C, lane, R, 31, 31, 0, 0), C.err);
+#endif
         fast_rounds<R>(w4, slab + base + lane * C.ncb, f, delta, C.ncb, lane, lanef, acc);
-    else
+    } else
         general_particle<R>(w4, g4, C, slab, quad, lane, acc, slow_count);
 }
 
@@ -285,6 +292,10 @@ __device__ __noinline__ float mean_value(const float4 w4, const float4 g4, const
     const int ka = node_pos(j, rec_bi(c0_bi), g4.y, g4.z, g4.w, fa);
     const int kb = node_pos(j + 1, rec_bi(c0_bi), g4.y, g4.z, g4.w, fb);
     auto node = [&](int k) {
+#if RUBIX_DEBUG
+        if (use_slab)
+            dbg_check((unsigned)((k - C.klo) * C.ncb + (cell - C.cell0)) < (unsigned)(C.slab_w * C.ncb), C.err);
+#endif
         const float4 q = use_slab ? slab[(k - C.klo) * C.ncb + (cell - C.cell0)]
                                   : quad_global(quad, C, cell, k);
         return quad_dot(w4, q);
@@ -327,9 +338,12 @@ __device__ __forceinline__ void mean_particle(const float4 w4, const float4 g4, 
                                               unsigned long long* slow_count) {
     int base;
     float f, delta;
-    if (fast_setup<R, 1>(g4, C, base, f, delta))
+    if (fast_setup<R, 1>(g4, C, base, f, delta)) {
+#if RUBIX_DEBUG
+        dbg_check(dbg_rounds_in_slab(base, f, delta, C, lane, R + 1, 30, R + 1, 0, 0), C.err);
+#endif
         mean_rounds<R>(w4, slab + base + lane * C.ncb, f, delta, C.ncb, lane, lanef, acc);
-    else
+    } else
         mean_general_particle<R>(w4, g4, C, slab, quad, lane, acc, slow_count);
 }
 
@@ -427,6 +441,9 @@ __global__ void __launch_bounds__(RUBIX_DEP_THREADS, RUBIX_DEP_CTAS) k_deposit(c
     C.n_cells = P.n_cells;
     C.q16 = P.quad16;
     C.qdt = P.qdt;
+#if RUBIX_DEBUG
+    C.err = P.err;
+#endif
     const uint32_t slab_bytes = (uint32_t)P.n_boxes * (uint32_t)P.box_w * (uint32_t)P.ncb * sizeof(float4);
     uint32_t phase = 0;
 

@@ -37,7 +37,35 @@ struct TileCtx {
     int j0, klo, slab_w, ncb, cell0, n_lambda, n_ls, n_cells;
     const uint2* q16;  // 16-bit cell quads (qdt 1: BF16, 2: FP16); null: FP32 quads
     int qdt;
+#if RUBIX_DEBUG
+    unsigned* err;     // error word for the debug build's index checks
+#endif
 };
+
+#if RUBIX_DEBUG
+// Debug builds: the slab nodes the fast-path rounds of one particle will
+// read, replayed with the rounds' own carry arithmetic (rounds of `step`
+// bins; node K0 + o_r + lane for r < n_rounds, the last round read by lanes
+// up to last_lanes only, plus the neighbours lo .. hi of each node) lie
+// inside the slab.
+__device__ __forceinline__ bool dbg_rounds_in_slab(int base, float f, float delta, const TileCtx& C, int lane,
+                                                   int n_rounds, int step, int last_lanes, int lo, int hi) {
+    const float d = (float)step * delta;
+    const int n = C.slab_w * C.ncb;
+    bool ok = true;
+    int o = 0;
+    for (int r = 0; r < n_rounds; ++r) {
+        if (r < n_rounds - 1 || lane <= last_lanes) {
+            ok = ok && base + (o + lane + lo) * C.ncb >= 0 && base + (o + lane + hi) * C.ncb < n;
+        }
+        f -= d;
+        const bool carry = f < 0.f;
+        f = carry ? f + 1.f : f;
+        o += carry ? step - 1 : step;
+    }
+    return ok;
+}
+#endif
 
 // The four corner templates of a 16-bit cell quad (x = corners 0 | 1 << 16,
 // y = corners 2 | 3 << 16) as FP32 values (exact).
