@@ -38,8 +38,11 @@
 //
 // Spaxels with more than `chunk` particles are split into several items whose
 // FP32 partial rows K5 (rows.cu) adds in item order, so the cube is bitwise
-// reproducible; later age bands add into the rows by L2 reductions in band
-// order (one per address and band, bands separated by the CTA barrier).
+// reproducible. Each later age band continues the row the earlier bands left:
+// the warp that owns the item in that band loads the row segment into its
+// accumulators before its particles and stores it back after them (plain
+// loads and stores, no atomics; one owner per row and band, bands separated
+// by the CTA barrier, so the order of every addition is fixed).
 #include "common.cuh"
 #include "kernels.h"
 #include "tile.cuh"
@@ -365,17 +368,25 @@ __global__ void k_job_cost(const DepositParams P, long long* job_cost) {
 constexpr int kJobChunk = 32;  // jobs per shared-memory work table
 
 // One work item's particles [q0, q1) of the current band, accumulated in
-// registers in sorted order, then stored (band 0) or added (later bands) to
-// the item's row dst. MEAN: bin means (rounds of 30 bins, R + 1 of them),
-// else centre samples (R rounds of 31).
+// registers in sorted order onto the item's row dst (zero for band 0, the
+// earlier bands' sum for later bands), then stored. MEAN: bin means (rounds
+// of 30 bins, R + 1 of them), else centre samples (R rounds of 31).
 template <int R, bool MEAN>
 __device__ __forceinline__ void deposit_item(const DepositParams& P, const TileCtx& C, const float4* __restrict__ rec4,
                                              int q0, int q1, float* dst, int band, const float4* __restrict__ slab,
                                              int lane, float lanef) {
     constexpr int NR = MEAN ? R + 1 : R;
     float acc[NR];
+    // band 0 starts the row from zero; later bands continue the row the
+    // earlier bands left (loaded now, in flight while the first particle's
+    // record and setup are prepared), so the row is written back with plain
+    // stores and no atomics
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0.f;
+    for (int r = 0; r < NR; ++r) {
+        const int j = MEAN ? C.j0 + 30 * r + lane : C.j0 + 31 * r + lane;
+        const bool owned = MEAN ? lane < (r < R ? 30 : R) : lane < 31;
+        acc[r] = (band > 0 && owned && j < P.n_lambda) ? dst[j] : 0.f;
+    }
     // the next particle's record is pulled into L1 while the current one is
     // deposited (no registers held across the particle)
     if (q0 < q1) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec4 + 2 * q0));
@@ -391,15 +402,7 @@ __device__ __forceinline__ void deposit_item(const DepositParams& P, const TileC
     for (int r = 0; r < NR; ++r) {
         const int j = MEAN ? C.j0 + 30 * r + lane : C.j0 + 31 * r + lane;
         const bool owned = MEAN ? lane < (r < R ? 30 : R) : lane < 31;
-        if (owned && j < P.n_lambda) {
-            if (band == 0) {
-                dst[j] = acc[r];
-            } else {
-                // one reduction per address and band, bands ordered by the
-                // CTA barrier: the sum order is fixed
-                atomicAdd(dst + j, acc[r]);
-            }
-        }
+        if (owned && j < P.n_lambda) dst[j] = acc[r];
     }
 }
 
