@@ -227,7 +227,9 @@ rubix_status rubix_cube_profile_history(rubix_cube_t *h, int32_t stage, float *m
  * field, [1] deposits = in-field particles * n_lambda, [2] (particle, tile)
  * pairs on the global-memory path (Doppler shift beyond the slab halo),
  * [3] deposit launches, [4] kernels launched by the forward, [5] device error
- * word (0 = none), [6] output bins per wavelength tile, [7] SSP nodes per
+ * word (0 = none; bits: 1 a bounded wait on a slab load expired, 2 a work
+ * item pointed outside its buffers, 4 an index check of the bounds-checking
+ * build failed), [6] output bins per wavelength tile, [7] SSP nodes per
  * shared-memory slab row, [8] age bands of the template grid.
  * n_inout: capacity in, number written out. */
 rubix_status rubix_cube_stats(rubix_cube_t *h, int64_t *stats, int32_t *n_inout);
